@@ -1,0 +1,128 @@
+"""Pins for the oracle's butterfly (Sec. 2.2, steps 1-4) against the paper and the
+mathematics: its error against the pinned direct sum lies in the paper's printed eps_a
+band (Tables 1-4) and falls with p; it is exact when the method is (N = 1 with sources
+on the grid nodes); the Kronecker form of M and E equals the dense p^d x p^d form; and
+planted mistakes (a wrong sign, a transposed factor, an off-by-one grid spacing) fail."""
+import numpy as np
+import pytest
+
+import oracle.butterfly as ob
+from conftest import paper_eps_bands, rel_l2
+from oracle.direct import direct
+from paper_0801_1524_gb300 import workloads as w
+
+BANDS = paper_eps_bands()
+
+
+def _curves(N):
+    x = w.sample_curve(w.circle_curve(), N)
+    k = w.sample_curve(w.perturbed_ellipse_curve(), N)
+    return x, k, w.gaussian_sources(k.shape[0], seed=0)[0]
+
+
+def test_golden_file_has_all_tables():
+    assert set(BANDS) == {(2, 5), (2, 7), (2, 9), (3, 5), (3, 7), (3, 9)}
+    assert BANDS[(2, 7)] == (7.81e-6, 1.18e-5)          # Tables 1 and 2, p = 7
+
+
+@pytest.mark.parametrize("p", [5, 7, 9])
+def test_2d_error_in_paper_band(p):
+    N = 1024.0
+    x, k, f = _curves(N)
+    eps = rel_l2(ob.butterfly(x, k, f, N, p), direct(x, k, f, N))
+    lo, hi = BANDS[(2, p)]
+    # The band transfers across curves and N (the paper finds eps_a flat in N); the
+    # floor catches an oracle that silently returns the exact sum.
+    assert lo / 8 < eps < 2 * hi, eps
+
+
+@pytest.mark.parametrize("p", [5, 7])
+def test_3d_error_in_paper_band(p):
+    N = 16.0
+    x = w.fibonacci_sphere(N)
+    f = w.gaussian_sources(x.shape[0], seed=1)[0]
+    eps = rel_l2(ob.butterfly(x, x, f, N, p), direct(x, x, f, N))
+    lo, hi = BANDS[(3, p)]
+    # A sphere against a sphere is smoother than the paper's aircraft and submarine
+    # surfaces, so the floor is looser than in 2D.
+    assert lo / 25 < eps < 2 * hi, eps
+
+
+def test_error_falls_with_p():
+    N = 256.0
+    x, k, f = _curves(N)
+    ref = direct(x, k, f, N)
+    errs = [rel_l2(ob.butterfly(x, k, f, N, p), ref) for p in (3, 5, 7, 9)]
+    assert all(a > 10 * b for a, b in zip(errs, errs[1:])), errs
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_exact_for_one_box_with_sources_on_nodes(dim):
+    # N = 1: one level, leaf = root.  Sources on the charge grid l/(p-1) make the
+    # equivalent charges equal the sources, and step 4 evaluates them exactly.
+    p = 5
+    q = p - 1
+    nodes = np.stack(np.meshgrid(*[np.arange(p) / q] * dim, indexing="ij"), -1).reshape(-1, dim)
+    rng = np.random.default_rng(2)
+    k = nodes[rng.choice(nodes.shape[0], size=nodes.shape[0] // 2, replace=False)]
+    x = rng.uniform(0, 1, (40, dim))
+    f = w.gaussian_sources(k.shape[0], seed=3)[0]
+    assert rel_l2(ob.butterfly(x, k, f, 1.0, p), direct(x, k, f, 1.0)) < 1e-12
+
+
+@pytest.mark.parametrize("dim,N,p", [(2, 8.0, 5), (3, 4.0, 3), (2, 16.0, 7)])
+def test_kronecker_form_equals_dense(dim, N, p):
+    inst = w.small_random(dim, N, p, nx=30, nk=25, seed=7)
+    f = inst.sources()[0]
+    a = ob.butterfly(inst.x, inst.k, f, N, p, dense=True)
+    b = ob.butterfly(inst.x, inst.k, f, N, p)
+    assert rel_l2(b, a) < 1e-12
+
+
+def test_linear_and_multi_rhs():
+    N = 64.0
+    inst = w.small_random(2, N, 5, nx=70, nk=60, seed=9)
+    f = inst.sources(nrhs=2)
+    u = ob.butterfly(inst.x, inst.k, f, N, 5)
+    comb = ob.butterfly(inst.x, inst.k, 2.0 * f[0] - 3j * f[1], N, 5)
+    assert rel_l2(comb, 2.0 * u[0] - 3j * u[1]) < 1e-12
+    assert rel_l2(u[1], ob.butterfly(inst.x, inst.k, f[1], N, 5)) < 1e-14
+
+
+def test_edge_points_and_far_corner():
+    # Points on box edges and exactly at N (clamped into the last box) stay accurate.
+    N = 32.0
+    inst = w.small_random(2, N, 7, nx=80, nk=80, seed=13, edge_fraction=0.5)
+    f = inst.sources()[0]
+    eps = rel_l2(ob.butterfly(inst.x, inst.k, f, N, 7), direct(inst.x, inst.k, f, N))
+    assert eps < 2 * BANDS[(2, 7)][1]
+
+
+def test_pair_counts_follow_levels():
+    N = 256.0
+    x, k, _ = _curves(N)
+    pc = ob.pair_counts(x, k, N)
+    L = 8
+    assert pc[L][0] == 1 and pc[0][1] == 1            # leaf step: A0; final step: B0
+    # Sec. 2.2: O(N) pairs per level for curves (boxes of width w: O(N/w) non-empty).
+    assert max(a * b for a, b in pc.values()) < 16 * N
+
+
+@pytest.mark.parametrize("mistake", ["sign", "transpose", "spacing"])
+def test_planted_mistakes_fail_the_band(monkeypatch, mistake):
+    N = 128.0
+    x, k, f = _curves(N)
+    ref = direct(x, k, f, N)
+    if mistake == "sign":
+        monkeypatch.setattr(ob, "cis", lambda phi: np.exp(-2j * np.pi * (np.asarray(phi) - np.floor(phi))))
+    elif mistake == "transpose":
+        orig = ob._axis_matrices
+        monkeypatch.setattr(ob, "_axis_matrices",
+                            lambda xg, kg, NN: [np.swapaxes(m, 1, 2) for m in orig(xg, kg, NN)])
+    else:
+        # grid step w/p instead of w/(p-1): the grid no longer reaches the far edge
+        monkeypatch.setattr(ob.Tree, "grid_1d",
+                            lambda self, s, p: self.corner(s)[:, :, None]
+                            + (np.arange(p) * (self.width[s] / p))[None, None, :])
+    eps = rel_l2(ob.butterfly(x, k, f, N, 7), ref)
+    assert eps > 2 * BANDS[(2, 7)][1], eps            # the band test would fail
