@@ -1,0 +1,414 @@
+#!/usr/bin/env python3
+"""Benchmark of the butterfly sparse Fourier transform on one GB300.
+
+Workload (one "step" = one whole transform: leaf step, the L recursive stages, final
+step): 2D, N = 8192, X = circle of radius 0.4 (82,355 targets), K = ellipse 0.45 x 0.3
+with a 0.03 sin(5 theta) radial perturbation (80,962 sources), p = 7, one right-hand side
+of complex64 Gaussian sources, FP32 arithmetic with FP64-built operators.
+
+Printed: one JSON line with transforms/s (device time, inputs resident), the same through
+the host-buffer C-ABI call (e2e), the roofline of the recursive-step kernel, the plain
+FP64 GPU butterfly and GPU direct sums on the same plan, and the oracle's CPU direct sum
+timed on the host cores.  `--impl reference` times the oracle alone.
+Under torchrun with N > 1 every rank runs an independent replica (the single transform
+is not sharded); value = transforms of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "transforms/sec and effective |I|*|J|/time vs plain FP64 GPU butterfly at rel L2 err<=1e-6"
+FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM (Blackwell)
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["bfly", "reference"], default="bfly")
+    ap.add_argument("--workload", default="curve8192")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="target wall time of the oracle CPU baseline sample")
+    ap.add_argument("--no-baselines", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(name):
+    from paper_0801_1524_gb300 import workloads as w
+    return w.WORKLOADS[name]()
+
+
+def describe(inst):
+    return {"workload": f"{inst.name}: {inst.dim}D, N={int(inst.N)}, p={inst.p}, "
+                        f"{inst.x.shape[0]} targets, {inst.k.shape[0]} sources, 1 RHS, "
+                        "complex64 Gaussian sources (seed 0)",
+            "N": int(inst.N), "p": inst.p, "dim": inst.dim, "nx": int(inst.x.shape[0]),
+            "nk": int(inst.k.shape[0]), "nrhs": 1,
+            "l2": "flushed between steps (256 MB write); per-step CUDA events"}
+
+
+# ---------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        self.t_on = self.t_off = None
+
+    def mark(self, on: bool):
+        if on:
+            self.t_on = time.time()
+        else:
+            self.t_off = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        mx = [num(r[2]) for r in rows if num(r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        loaded = [s for s in sm if mx and s >= 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- oracle
+def oracle_direct_rate(inst, f, seconds: float, seed: int = 12345):
+    """The oracle's FP64 direct sum (eq. 1.1) on a seeded subset S of the targets, sized
+    to about `seconds` of host time; returns (transforms/s extrapolated, |S|, threads, s)."""
+    from oracle.direct import direct, threads
+    rng = np.random.default_rng(seed)
+    nx = inst.x.shape[0]
+    order = rng.permutation(nx)
+    probe = order[:min(nx, 256)]
+    t0 = time.perf_counter()
+    direct(inst.x[probe], inst.k, f, inst.N)
+    per_target = (time.perf_counter() - t0) / len(probe)
+    m = int(min(nx, max(256, seconds / max(per_target, 1e-9))))
+    S = order[:m]
+    t0 = time.perf_counter()
+    direct(inst.x[S], inst.k, f, inst.N)
+    dt = time.perf_counter() - t0
+    return (m / nx) / dt, m, threads(), dt
+
+
+# ---------------------------------------------------------------------------- main arm
+def main_bfly(args, rank, world, dist):
+    import torch
+    from paper_0801_1524_gb300.plan import Plan
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    inst = workload(args.workload)
+    nx, nk = inst.x.shape[0], inst.k.shape[0]
+    f_np = inst.sources(dtype=np.complex64)[0]
+    stream = torch.cuda.current_stream()
+    f = torch.as_tensor(f_np, device=dev)
+    plan = Plan(inst.x, inst.k, inst.N, inst.p, precision="fp32")
+    info = plan.info()
+    L = info["L"]
+    u = torch.empty(nx, dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def new_events():
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(L + 3)]
+        for e in evs:
+            e.record(stream)
+        return evs
+
+    # warm-up
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        plan.forward(f, out=u)
+    torch.cuda.synchronize()
+
+    events = [new_events() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    gpu_index = int(vis[local]) if local < len(vis) and vis[local].strip().isdigit() else local
+    clocks = Clocks(gpu_index) if rank == 0 else None
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.mark(True)
+    for k in range(args.steps):
+        flush.zero_()
+        plan.with_events(f, events[k], out=u)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.mark(False)
+    step_ms = [ev[0].elapsed_time(ev[L + 2]) for ev in events]
+    level_ms = [ev[1].elapsed_time(ev[L + 1]) for ev in events]
+    kern_ms = np.array([[ev[i].elapsed_time(ev[i + 1]) for i in range(L + 2)] for ev in events])
+    ms = float(np.mean(step_ms))
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clk = clocks.stop() if clocks else None
+
+    # ---- end to end through the host-buffer C-ABI call (copies inside the timed call)
+    f_pin = torch.empty(nk, dtype=torch.complex64).pin_memory()
+    f_pin.copy_(torch.as_tensor(f_np))
+    u_pin = torch.empty(nx, dtype=torch.complex64).pin_memory()
+    f_host = f_pin.numpy()
+    u_host = u_pin.numpy()
+    for _ in range(3):
+        plan.execute_host(f_host, out=u_host.reshape(1, -1))
+    e2e = []
+    for _ in range(max(10, min(args.steps, 100))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.execute_host(f_host, out=u_host.reshape(1, -1))
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e))
+
+    if rank != 0:
+        return None
+
+    # ---- accuracy of this run and baselines on the same GPU
+    out = {}
+    u32 = u.to(torch.complex128)
+    if not args.no_baselines:
+        plan64 = Plan(inst.x, inst.k, inst.N, inst.p, precision="fp64")
+        f64 = f.to(torch.complex128)
+        u64 = torch.empty(nx, dtype=torch.complex128, device=dev)
+        for _ in range(3):
+            plan64.forward(f64, out=u64)
+        torch.cuda.synchronize()
+        ev64 = []
+        for _ in range(min(args.steps, 20)):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan64.forward(f64, out=u64)
+            b.record(stream)
+            ev64.append((a, b))
+        torch.cuda.synchronize()
+        ms64 = float(np.mean([a.elapsed_time(b) for a, b in ev64]))
+        rel_vs_fp64 = (torch.linalg.norm(u32 - u64) / torch.linalg.norm(u64)).item()
+        # direct sums on the GPU (eq. 1.1), FP64 phase reduction
+        ud = torch.empty(nx, dtype=torch.complex128, device=dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan64.direct(f64, out=ud)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_direct64 = a.elapsed_time(b)
+        ud32 = torch.empty(nx, dtype=torch.complex64, device=dev)
+        a.record(stream)
+        plan.direct(f, out=ud32)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_direct32 = a.elapsed_time(b)
+        eps_a = (torch.linalg.norm(u64 - ud) / torch.linalg.norm(ud)).item()
+        eps_a32 = (torch.linalg.norm(u32 - ud) / torch.linalg.norm(ud)).item()
+        out["baselines"] = {
+            "fp64_gpu_butterfly": {"ms": ms64, "transforms_per_s": 1e3 / ms64,
+                                   "speedup_of_fp32_path": ms64 / ms},
+            "gpu_direct_fp64": {"ms": ms_direct64, "transforms_per_s": 1e3 / ms_direct64},
+            "gpu_direct_fp32": {"ms": ms_direct32, "transforms_per_s": 1e3 / ms_direct32},
+        }
+        out["accuracy"] = {"rel_l2_fp32_vs_fp64_butterfly": rel_vs_fp64,
+                           "gate_1e-6_met": rel_vs_fp64 <= 1e-6,
+                           "eps_a_fp64_vs_gpu_direct_fp64": eps_a,
+                           "eps_a_fp32_vs_gpu_direct_fp64": eps_a32}
+        del plan64
+
+    # ---- roofline of the recursive step (the dominant kernel: L launches per step)
+    d, p = inst.dim, inst.p
+    PD = p ** d
+    flops = info["jobs_fwd"] * d * p ** (d + 1) * 8.0              # real flops, all stages
+    bytes_ = (info["tiles_read_fwd"] + info["tiles_written_fwd"]) * PD * 8.0
+    level_s = float(np.mean(level_ms)) * 1e-3
+    per_launch_s = level_s / L
+    hbm_peak, hbm_src = peaks()
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
+    a_alu = flops / L / per_launch_s / 1e12
+    a_hbm = bytes_ / L / per_launch_s / 1e9
+    roof_alu = {"bound": "alu", "achieved": a_alu, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": a_alu / alu_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    roof_hbm = {"bound": "hbm", "achieved": a_hbm, "peak": hbm_peak, "unit": "GB/s",
+                "frac": a_hbm / hbm_peak, "traffic": None,
+                "peak_source": f"{hbm_src} copy bandwidth"}
+    traffic = level_traffic(per_launch_bytes=bytes_ / L)
+    main, alt = (roof_alu, roof_hbm) if roof_alu["frac"] >= roof_hbm["frac"] else (roof_hbm, roof_alu)
+    main["traffic"] = traffic
+    alt["traffic"] = traffic
+    main["kernel"] = "level_kernel<float,2,7,fwd> (recursive step, one launch per stage)"
+    main["algorithmic_per_launch"] = {"flops": flops / L, "bytes": bytes_ / L}
+    out["roofline_alt"] = alt
+    kern_names = ["leaf"] + [f"level_t{t}" for t in range(L - 1, -1, -1)] + ["final"]
+    out["kernel_ms"] = {n: float(v) for n, v in zip(kern_names, kern_ms.mean(axis=0))}
+
+    value = world * 1e3 / ms
+    line = {
+        "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {**describe(inst), "parallelism": f"replicas{world}" if world > 1 else "single GPU",
+                   "precision": "FP32 applies, FP64-built operators and weights"},
+        "effective_IJ_per_s": value * nx * nk,
+        "e2e": {"value": world / e2e_s, "unit": "transforms/s", "h2d_bytes_per_step": nk * 8,
+                "d2h_bytes_per_step": nx * 8, "ms": e2e_s * 1e3,
+                "call": "bfly_execute_host (pinned host buffers)"},
+        "roofline": main,
+        "gpu_launches": args.steps * (L + 2),
+        "clocks": clk,
+        "plan": {"seconds": info["plan_seconds"], "L": L, "total_pairs": info["total_pairs"],
+                 "max_pairs": info["max_pairs"], "workspace_bytes": info["workspace_bytes"]},
+    }
+    line.update(out)
+    if not args.no_baselines:
+        rate, m, thr, dt = oracle_direct_rate(inst, f_np.astype(np.complex128), args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "transforms/s", "cores": thr, "kind": "oracle",
+                                "sample": f"FP64 direct sum (eq. 1.1) over {m} of {nx} targets "
+                                          f"(seeded), all {nk} sources, {dt:.1f} s, "
+                                          "extrapolated x nx/|S|"}
+    return line
+
+
+def level_traffic(per_launch_bytes):
+    """DRAM bytes per recursive-step launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "level_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        import hashlib
+        src = os.path.join(ROOT, "paper_0801_1524_gb300", "csrc", "level.cuh")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if d.get("level_cuh_sha256_16") != h:
+            return None
+        return float(d["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------- reference arm
+def main_reference(args, rank):
+    if rank != 0:
+        return None
+    inst = workload(args.workload)
+    f = inst.sources(dtype=np.complex128)[0]
+    per_step = max(1.0, min(8.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_direct_rate(inst, f, per_step / 4)
+    rates, thr, m = [], 0, 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        r, m, thr, _ = oracle_direct_rate(inst, f, per_step, seed=12345 + k)
+        rates.append(r)
+    wall = time.perf_counter() - t0
+    value = float(np.mean(rates))
+    sample = (f"FP64 direct sum (eq. 1.1) over about {m} of {inst.x.shape[0]} targets per step "
+              f"(seeded), all {inst.k.shape[0]} sources, extrapolated x nx/|S|")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": describe(inst),
+            "cpu_baseline": {"value": value, "unit": "transforms/s", "cores": thr, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "bfly":
+        import __graft_entry__
+        __graft_entry__.build()
+    if world > 1 and args.impl == "bfly":
+        import torch
+        import torch.distributed as tdist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group(backend)
+        dist = tdist
+    if args.impl == "reference":
+        line = main_reference(args, rank)
+    else:
+        line = main_bfly(args, rank, world, dist)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

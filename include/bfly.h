@@ -1,0 +1,169 @@
+/*
+ * bfly.h — C ABI of the GB300 butterfly sparse Fourier transform.
+ *
+ * The transform (eq. 1.1, Sec. 1):   u_i = sum_j exp(2 pi i x_i . k_j / N) f_j
+ * for targets x_i and sources k_j in [0, N]^dim (dim = 2 or 3), computed by the
+ * butterfly algorithm of Sec. 2.2 with p^dim equivalent charges per box pair.
+ *
+ * Conventions shared by every entry point
+ *   - Complex arrays are interleaved (re, im) pairs: complex64 (BFLY_C64, two floats) or
+ *     complex128 (BFLY_C128, two doubles).  A batch of nrhs right-hand sides is stored
+ *     right-hand side major: f[r][j] at f + r*nk, u[r][i] at u + r*nx (in elements).
+ *   - Points are row-major doubles, x[i*dim + d], in the caller's order; results come
+ *     back in the caller's order.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
+ *     Execution entry points are asynchronous on that stream and never synchronise the
+ *     device, except bfly_execute_host (which returns once its result is on the host).
+ *   - No entry point throws; every failure returns a status and records a message that
+ *     bfly_last_error() returns (thread-local, valid until the next call on the thread).
+ *   - A plan may be used by one stream at a time: its workspace is shared by its calls.
+ */
+#ifndef BFLY_H
+#define BFLY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bfly_plan_s *bfly_plan_t;
+
+typedef enum {
+  BFLY_OK = 0,
+  BFLY_ERR_INVALID_ARG = 1,   /* bad dimension, p, N, point, pointer or size */
+  BFLY_ERR_OUT_OF_MEMORY = 2, /* a host or device allocation failed */
+  BFLY_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
+  BFLY_ERR_UNSUPPORTED = 4,   /* valid request outside what this build implements */
+  BFLY_ERR_TIMEOUT = 5        /* a bounded device-side wait gave up */
+} bfly_status;
+
+typedef enum { BFLY_C64 = 0, BFLY_C128 = 1 } bfly_dtype;
+
+/* Arithmetic of the butterfly applies.  FP32: complex64 charges, FP32 operators and
+ * accumulation, operators and per-point weights built in FP64.  FP64: complex128
+ * throughout (the plain FP64 GPU butterfly). */
+typedef enum { BFLY_PREC_FP64 = 0, BFLY_PREC_FP32 = 1 } bfly_precision;
+
+/* Build only the host plan: no device memory is touched, execution entry points return
+ * BFLY_ERR_INVALID_ARG; bfly_plan_info and bfly_plan_stage still work.  */
+#define BFLY_FLAG_HOST_ONLY 1u
+
+typedef struct {
+  int prec;          /* bfly_precision; default BFLY_PREC_FP32 */
+  int max_nrhs;      /* workspace is sized for up to this many right-hand sides (>= 1) */
+  unsigned flags;    /* BFLY_FLAG_* */
+  int smem_kb;       /* shared memory per block for the recursive step, 0 = default */
+  int reserved[4];   /* must be zero */
+} bfly_opts;
+
+typedef struct {
+  int dim, p, L;                /* L = log2 N levels below the root */
+  int prec;                     /* bfly_precision of the plan */
+  double N;
+  int64_t nx, nk;               /* number of targets and sources */
+  int64_t total_pairs;          /* sum over stages t of nA(L-t) * nK(t) */
+  int64_t max_pairs;            /* largest stage */
+  int64_t workspace_bytes;      /* device bytes held by the plan */
+  int64_t tiles_read_fwd;       /* recursive step: charge tiles read, forward, one RHS */
+  int64_t tiles_written_fwd;    /* recursive step: charge tiles written, forward */
+  int64_t jobs_fwd;             /* (output box pair, child) contractions, forward */
+  int64_t chunks_fwd;           /* blocks of work of the recursive step, all stages */
+  double plan_seconds;          /* host wall time of bfly_plan_create */
+} bfly_plan_info_t;
+
+/*
+ * bfly_plan_create — Sec. 2.2 step 1 and everything that depends only on the points:
+ * scales nothing (the points are already in [0,N]^dim), assigns every point to its unit
+ * leaf box (index min(floor(x), N-1) per axis), sorts the points by leaf in Morton
+ * order, builds the non-empty boxes of every level of T_X and T_K with their child
+ * ranges, the transfer operators (eqs. M1 and E1 combined, built in FP64), and the
+ * per-point interpolation weights of steps 2 and 4; uploads all of it and allocates two
+ * charge buffers of the largest stage (Sec. 2.2: two adjacent levels are live).
+ *   out      receives the plan; *out is NULL on failure.
+ *   dim      2 or 3.   N: a power of two >= 1.   p: 3, 5, 7 or 9.
+ *   x, k     host arrays [nx][dim] and [nk][dim], every coordinate finite and in [0,N];
+ *            copied, the caller keeps ownership.  nx, nk >= 1.
+ *   opts     NULL for defaults.
+ * Errors: INVALID_ARG (any of the above), UNSUPPORTED (N not a power of two; a p or
+ * precision whose workspace does not fit on chip), OUT_OF_MEMORY, CUDA.
+ * The device current at the call owns the plan's memory; execute on that device.
+ */
+bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx,
+                             const double *x, int64_t nk, const double *k, int p,
+                             const bfly_opts *opts);
+
+/* Frees the plan and its device memory (after synchronising with nothing: the caller
+ * must ensure no execution on the plan is in flight).  NULL is ignored. */
+void bfly_plan_destroy(bfly_plan_t plan);
+
+/*
+ * bfly_execute — the forward transform, Sec. 2.2 steps 2-4: leaf equivalent charges,
+ * the recursive step for t = L-1 .. 0, and evaluation at the targets.
+ *   f   device [nrhs][nk] sources (dtype), read only.
+ *   u   device [nrhs][nx] potentials (dtype), overwritten.
+ *   1 <= nrhs <= max_nrhs of the plan.  f and u must not overlap.
+ * The arithmetic is the plan's precision whatever the I/O dtype.
+ */
+bfly_status bfly_execute(bfly_plan_t plan, const void *f, void *u, int nrhs, int dtype,
+                         void *stream);
+
+/*
+ * bfly_execute_adjoint — the exact conjugate transpose of bfly_execute (the same sweep
+ * run backwards, T_X to T_K, with conjugate-transposed operators):
+ *   f_j ~= sum_i exp(-2 pi i x_i . k_j / N) u_i.
+ *   u   device [nrhs][nx] input;  f  device [nrhs][nk] output, overwritten.
+ */
+bfly_status bfly_execute_adjoint(bfly_plan_t plan, const void *u, void *f, int nrhs,
+                                 int dtype, void *stream);
+
+/*
+ * bfly_execute_host — bfly_execute (adjoint = 0) or bfly_execute_adjoint (adjoint = 1)
+ * on HOST buffers: copies the input to the plan's device staging buffer, runs the sweep,
+ * copies the result back and waits for it.  Pinned host memory gives asynchronous copies;
+ * pageable memory works too.  in: [nrhs][nk] (forward) or [nrhs][nx] (adjoint).
+ */
+bfly_status bfly_execute_host(bfly_plan_t plan, const void *in_host, void *out_host,
+                              int nrhs, int dtype, int adjoint, void *stream);
+
+/*
+ * bfly_direct — eq. 1.1 summed term by term on the GPU (O(nx*nk)), the exact reference
+ * and the GPU direct-sum baseline.  The phase x.k/N is formed and reduced mod 1 in FP64;
+ * the exponential is evaluated in the plan's precision, sums are FP32 within tiles of
+ * sources and FP64 across tiles for an FP32 plan, FP64 throughout for an FP64 plan.
+ *   adjoint = 0: in = f [nrhs][nk] -> out = u [nrhs][nx];
+ *   adjoint = 1: in = u [nrhs][nx] -> out = f [nrhs][nk] with exp(-2 pi i x.k/N).
+ */
+bfly_status bfly_direct(bfly_plan_t plan, const void *in, void *out, int nrhs, int dtype,
+                        int adjoint, void *stream);
+
+/*
+ * bfly_execute_events — bfly_execute (adjoint = 0) or bfly_execute_adjoint (adjoint = 1)
+ * that also records caller-owned CUDA events on `stream`: events[i] just before kernel
+ * launch i and events[L+2] after the last launch, so that the elapsed time between
+ * events[i] and events[i+1] is the device time of launch i.  Launch order: forward [leaf
+ * step, recursive step t = L-1 .. 0, final step]; adjoint [final step adjoint, recursive
+ * step t = 0 .. L-1, leaf step adjoint].  n_events must be L + 3; NULL entries are
+ * skipped.  Asynchronous like bfly_execute: nothing is synchronised or allocated.
+ */
+bfly_status bfly_execute_events(bfly_plan_t plan, const void *in, void *out, int nrhs,
+                                int dtype, int adjoint, void *stream, void *const *events,
+                                int n_events);
+
+/* Sizes and counts of the plan (host data; no device access). */
+bfly_status bfly_plan_info(bfly_plan_t plan, bfly_plan_info_t *info);
+
+/* Stage t (0..L): number of non-empty T_X boxes at level L-t (nA) and T_K boxes at
+ * level t (nB); the stage holds nA*nB equivalent-charge tiles. */
+bfly_status bfly_plan_stage(bfly_plan_t plan, int t, int64_t *nA, int64_t *nB);
+
+/* Message of the last failure on this thread ("" if none). */
+const char *bfly_last_error(void);
+
+/* Build identification, e.g. "bfly 0.1 sm_103a". */
+const char *bfly_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BFLY_H */

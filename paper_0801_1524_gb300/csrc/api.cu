@@ -1,0 +1,557 @@
+// C ABI of the butterfly (include/bfly.h): plan creation, upload and the execution entry
+// points.  Every step of the transform runs in the kernels of this library.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/bfly.h"
+#include "kernels.hpp"
+#include "plan.hpp"
+
+using bfly::Chunk;
+using bfly::HostTree;
+using bfly::KernelSet;
+
+namespace {
+
+thread_local std::string g_err;
+
+bfly_status fail(bfly_status s, const std::string &msg) {
+  g_err = msg;
+  return s;
+}
+
+#define BFLY_CUDA(call)                                                                    \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? BFLY_ERR_OUT_OF_MEMORY : BFLY_ERR_CUDA, \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+const KernelSet *select_kernels(int p, int prec, int dim) {
+  switch (p) {
+    case 3: return bfly::kernels_p3(prec, dim);
+    case 5: return bfly::kernels_p5(prec, dim);
+    case 7: return bfly::kernels_p7(prec, dim);
+    case 9: return bfly::kernels_p9(prec, dim);
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+struct bfly_plan_s {
+  int dim = 0, p = 0, L = 0, prec = 1, max_nrhs = 1;
+  unsigned flags = 0;
+  double N = 0;
+  int64_t nx = 0, nk = 0;
+  int device = -1;
+  HostTree TX, TK;
+  const KernelSet *ks = nullptr;
+  int tile_cap = 0, level_grid = 0;
+  size_t level_smem = 0, elem_bytes = 0;
+  std::vector<std::vector<Chunk>> chf, cha;  // per stage t in [0, L-1]
+  std::vector<int64_t> pairs;                 // per stage t in [0, L]
+  // device memory: one allocation carved into the arrays below
+  char *dmem = nullptr;
+  size_t dbytes = 0;
+  int32_t *perm_x = nullptr, *perm_k = nullptr, *leaf_x = nullptr, *leaf_k = nullptr;
+  int32_t *pleaf_x = nullptr, *pleaf_k = nullptr, *lidx_x = nullptr;
+  double *off_x = nullptr, *off_k = nullptr, *xs = nullptr, *ks_ = nullptr, *inv_den = nullptr;
+  void *Wx = nullptr, *Wk = nullptr, *table = nullptr, *tableH = nullptr;
+  std::vector<int32_t *> xcs, kcs;       // level s in [0, L-1]
+  std::vector<uint32_t *> xcode, kcode;  // level s in [0, L] (0 unused)
+  std::vector<Chunk *> d_chf, d_cha;
+  void *buf[2] = {nullptr, nullptr};
+  void *stage_in = nullptr, *stage_out = nullptr;
+  bfly_plan_info_t info{};
+};
+
+namespace {
+
+// Collects the plan's device arrays, then makes one allocation and uploads them.
+struct Arena {
+  struct Item {
+    void **slot;
+    size_t bytes;
+    const void *host;
+  };
+  std::vector<Item> items;
+  size_t total = 0;
+  void add(void **slot, size_t bytes, const void *host = nullptr) {
+    items.push_back({slot, bytes, host});
+    total += (bytes + 255) & ~(size_t)255;
+  }
+  template <typename T>
+  void add_vec(T **slot, const std::vector<T> &v) {
+    add(reinterpret_cast<void **>(slot), v.size() * sizeof(T), v.data());
+  }
+};
+
+bool is_pow2(double N, int *L) {
+  if (!(N >= 1.0) || !std::isfinite(N)) return false;
+  int e = 0;
+  const double m = std::frexp(N, &e);
+  if (m != 0.5) return false;
+  *L = e - 1;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bfly_last_error(void) { return g_err.c_str(); }
+
+const char *bfly_version(void) { return "bfly 0.1 sm_103a"; }
+
+void bfly_plan_destroy(bfly_plan_t plan) {
+  if (!plan) return;
+  if (plan->dmem) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != plan->device) cudaSetDevice(plan->device);
+    cudaFree(plan->dmem);
+    if (cur != plan->device && cur >= 0) cudaSetDevice(cur);
+  }
+  delete plan;
+}
+
+bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, const double *x,
+                             int64_t nk, const double *k, int p, const bfly_opts *opts) {
+  g_err.clear();
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!out) return fail(BFLY_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return fail(BFLY_ERR_INVALID_ARG, "dim must be 2 or 3");
+  if (p < 3 || p > 9) return fail(BFLY_ERR_INVALID_ARG, "p must be in 3..9");
+  if (p % 2 == 0) return fail(BFLY_ERR_UNSUPPORTED, "this build has kernels for p = 3, 5, 7, 9");
+  if (!std::isfinite(N) || !(N > 0)) return fail(BFLY_ERR_INVALID_ARG, "N must be finite and > 0");
+  int L = 0;
+  if (!is_pow2(N, &L)) return fail(BFLY_ERR_UNSUPPORTED, "N must be a power of two >= 1");
+  if ((dim == 2 && L > 30) || (dim == 3 && L > 20))
+    return fail(BFLY_ERR_UNSUPPORTED, "N too large for 64-bit Morton keys");
+  if (nx < 1 || nk < 1 || nx > INT32_MAX / 2 || nk > INT32_MAX / 2)
+    return fail(BFLY_ERR_INVALID_ARG, "nx and nk must be in [1, 2^30)");
+  if (!x || !k) return fail(BFLY_ERR_INVALID_ARG, "x or k is NULL");
+  bfly_opts o{};
+  o.prec = BFLY_PREC_FP32;
+  o.max_nrhs = 1;
+  if (opts) o = *opts;
+  if (o.prec != BFLY_PREC_FP32 && o.prec != BFLY_PREC_FP64)
+    return fail(BFLY_ERR_INVALID_ARG, "unknown precision");
+  if (o.max_nrhs < 1 || o.max_nrhs > 4096) return fail(BFLY_ERR_INVALID_ARG, "max_nrhs must be in 1..4096");
+  for (int i = 0; i < 4; ++i)
+    if (o.reserved[i] != 0) return fail(BFLY_ERR_INVALID_ARG, "reserved options must be zero");
+
+  bfly_plan_t P = new (std::nothrow) bfly_plan_s();
+  if (!P) return fail(BFLY_ERR_OUT_OF_MEMORY, "host allocation");
+  P->dim = dim;
+  P->p = p;
+  P->L = L;
+  P->N = N;
+  P->nx = nx;
+  P->nk = nk;
+  P->prec = o.prec;
+  P->max_nrhs = o.max_nrhs;
+  P->flags = o.flags;
+  std::string err = bfly::build_tree(P->TX, dim, L, nx, x);
+  if (err.empty()) err = bfly::build_tree(P->TK, dim, L, nk, k);
+  if (!err.empty()) {
+    delete P;
+    return fail(BFLY_ERR_INVALID_ARG, err);
+  }
+  const int q = p - 1;
+  int PD = 1;
+  for (int d = 0; d < dim; ++d) PD *= p;
+  P->elem_bytes = o.prec == BFLY_PREC_FP64 ? 16 : 8;
+  // stage sizes: stage t pairs T_X level L-t with T_K level t
+  P->pairs.resize(L + 1);
+  int64_t maxp = 0, tot = 0;
+  for (int t = 0; t <= L; ++t) {
+    P->pairs[t] = P->TX.nbox(L - t) * P->TK.nbox(t);
+    maxp = std::max(maxp, P->pairs[t]);
+    tot += P->pairs[t];
+  }
+  bfly_plan_info_t &I = P->info;
+  I.dim = dim;
+  I.p = p;
+  I.L = L;
+  I.prec = o.prec;
+  I.N = N;
+  I.nx = nx;
+  I.nk = nk;
+  I.total_pairs = tot;
+  I.max_pairs = maxp;
+  for (int t = 0; t < L; ++t) {
+    I.tiles_read_fwd += P->pairs[t + 1];
+    I.tiles_written_fwd += P->pairs[t];
+    I.jobs_fwd += P->TX.nbox(L - t) * P->TK.nbox(t + 1);
+  }
+
+  const bool host_only = (o.flags & BFLY_FLAG_HOST_ONLY) != 0;
+  // shared memory plan of the recursive step
+  P->ks = select_kernels(p, o.prec == BFLY_PREC_FP64 ? 0 : 1, dim);
+  if (!P->ks) {
+    delete P;
+    return fail(BFLY_ERR_UNSUPPORTED, "no kernels for this (dim, p)");
+  }
+  size_t max_smem = 227 * 1024;
+  if (!host_only) {
+    int dev = 0, v = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) {
+      delete P;
+      return fail(BFLY_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e));
+    }
+    P->device = dev;
+    max_smem = (size_t)v;
+  }
+  const size_t want = (size_t)(o.smem_kb > 0 ? o.smem_kb : 100) * 1024;
+  const int min_tiles = 2 << dim;  // the largest unit with a single output
+  auto cap_for = [&](size_t budget) -> int {
+    if (budget <= P->ks->level_fixed_bytes + 64) return 0;
+    size_t c = (budget - P->ks->level_fixed_bytes - 64) / (P->ks->level_tile_bytes + 2);
+    return (int)std::min<size_t>(c, 65535);
+  };
+  int cap = cap_for(std::min(want, max_smem));
+  if (cap < min_tiles) cap = cap_for(max_smem);
+  if (cap < min_tiles) {
+    delete P;
+    return fail(BFLY_ERR_UNSUPPORTED, "charge tiles of this (dim, p, precision) do not fit in shared memory");
+  }
+  P->tile_cap = cap;
+  P->level_smem = P->ks->level_smem(cap);
+  P->chf.resize(L);
+  P->cha.resize(L);
+  for (int t = 0; t < L; ++t) {
+    P->chf[t] = bfly::make_chunks(P->TX.cs[L - t - 1], P->TK.cs[t], false, cap);
+    P->cha[t] = bfly::make_chunks(P->TX.cs[L - t - 1], P->TK.cs[t], true, cap);
+    I.chunks_fwd += (int64_t)P->chf[t].size();
+  }
+  if (host_only) {
+    I.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = P;
+    return BFLY_OK;
+  }
+
+  // ---- device arrays
+  std::vector<uint32_t> empty_code;
+  std::vector<std::vector<uint32_t>> xcode(L + 1), kcode(L + 1);
+  for (int s = 1; s <= L; ++s) {
+    const int64_t nxs = P->TX.nbox(s), nks = P->TK.nbox(s);
+    xcode[s].resize(nxs);
+    kcode[s].resize(nks);
+    for (int64_t i = 0; i < nxs; ++i) {
+      uint32_t c = 0;
+      for (int d = 0; d < dim; ++d) c |= (uint32_t)(P->TX.idx[s][i * dim + d] % (2 * q)) << (8 * d);
+      xcode[s][i] = c;
+    }
+    for (int64_t i = 0; i < nks; ++i) {
+      uint32_t c = 0;
+      for (int d = 0; d < dim; ++d) c |= (uint32_t)(P->TK.idx[s][i * dim + d] & 1) << d;
+      kcode[s][i] = c;
+    }
+  }
+  std::vector<double> inv_den(p);
+  for (int m = 0; m < p; ++m) {
+    double den = 1.0;
+    for (int n2 = 0; n2 < p; ++n2)
+      if (n2 != m) den *= std::sin(M_PI * (double)(m - n2) / ((double)q * q));
+    inv_den[m] = 1.0 / den;
+  }
+  std::vector<double> tabF = bfly::transfer_table(p, false), tabH = bfly::transfer_table(p, true);
+  std::vector<float> tabF32, tabH32;
+  if (o.prec == BFLY_PREC_FP32) {
+    tabF32.assign(tabF.begin(), tabF.end());
+    tabH32.assign(tabH.begin(), tabH.end());
+  }
+  std::vector<double> xs(x, x + nx * dim), kv(k, k + nk * dim);
+
+  Arena A;
+  A.add_vec(&P->perm_x, P->TX.perm);
+  A.add_vec(&P->perm_k, P->TK.perm);
+  A.add_vec(&P->leaf_x, P->TX.leaf_start);
+  A.add_vec(&P->leaf_k, P->TK.leaf_start);
+  A.add_vec(&P->pleaf_x, P->TX.point_leaf);
+  A.add_vec(&P->pleaf_k, P->TK.point_leaf);
+  A.add_vec(&P->lidx_x, P->TX.idx[L]);
+  A.add_vec(&P->off_x, P->TX.off);
+  A.add_vec(&P->off_k, P->TK.off);
+  A.add_vec(&P->xs, xs);
+  A.add_vec(&P->ks_, kv);
+  A.add_vec(&P->inv_den, inv_den);
+  if (o.prec == BFLY_PREC_FP32) {
+    A.add(&P->table, tabF32.size() * sizeof(float), tabF32.data());
+    A.add(&P->tableH, tabH32.size() * sizeof(float), tabH32.data());
+  } else {
+    A.add(&P->table, tabF.size() * sizeof(double), tabF.data());
+    A.add(&P->tableH, tabH.size() * sizeof(double), tabH.data());
+  }
+  A.add(&P->Wx, (size_t)nx * dim * p * P->elem_bytes);
+  A.add(&P->Wk, (size_t)nk * dim * p * P->elem_bytes);
+  P->xcs.assign(L, nullptr);
+  P->kcs.assign(L, nullptr);
+  P->xcode.assign(L + 1, nullptr);
+  P->kcode.assign(L + 1, nullptr);
+  P->d_chf.assign(L, nullptr);
+  P->d_cha.assign(L, nullptr);
+  for (int s = 0; s < L; ++s) {
+    A.add_vec(&P->xcs[s], P->TX.cs[s]);
+    A.add_vec(&P->kcs[s], P->TK.cs[s]);
+  }
+  for (int s = 1; s <= L; ++s) {
+    A.add_vec(&P->xcode[s], xcode[s]);
+    A.add_vec(&P->kcode[s], kcode[s]);
+  }
+  for (int t = 0; t < L; ++t) {
+    A.add_vec(&P->d_chf[t], P->chf[t]);
+    A.add_vec(&P->d_cha[t], P->cha[t]);
+  }
+  const size_t buf_bytes = (size_t)maxp * PD * P->elem_bytes * o.max_nrhs;
+  A.add(&P->buf[0], buf_bytes);
+  A.add(&P->buf[1], buf_bytes);
+  const size_t stage_bytes = (size_t)std::max(nx, nk) * 16 * o.max_nrhs;
+  A.add(&P->stage_in, stage_bytes);
+  A.add(&P->stage_out, stage_bytes);
+
+  cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&P->dmem), A.total);
+  if (e != cudaSuccess) {
+    delete P;
+    return fail(e == cudaErrorMemoryAllocation ? BFLY_ERR_OUT_OF_MEMORY : BFLY_ERR_CUDA,
+                std::string("cudaMalloc of the plan: ") + cudaGetErrorString(e));
+  }
+  P->dbytes = A.total;
+  size_t at = 0;
+  for (auto &it : A.items) {
+    *it.slot = P->dmem + at;
+    if (it.host && it.bytes) {
+      e = cudaMemcpy(*it.slot, it.host, it.bytes, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) break;
+    }
+    at += (it.bytes + 255) & ~(size_t)255;
+  }
+  if (e == cudaSuccess)
+    e = bfly::launch_weights(o.prec == BFLY_PREC_FP64 ? 0 : 1, nk, dim, p, 0, P->off_k, P->pleaf_k,
+                             nullptr, P->inv_den, P->Wk, 0);
+  if (e == cudaSuccess)
+    e = bfly::launch_weights(o.prec == BFLY_PREC_FP64 ? 0 : 1, nx, dim, p, 1, P->off_x, P->pleaf_x,
+                             P->lidx_x, P->inv_den, P->Wx, 0);
+  int blocks = 0;
+  if (e == cudaSuccess) e = P->ks->level_setup(P->level_smem, &blocks);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int sms = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+  if (e != cudaSuccess) {
+    const std::string msg = std::string("plan upload: ") + cudaGetErrorString(e);
+    bfly_plan_destroy(P);
+    return fail(BFLY_ERR_CUDA, msg);
+  }
+  if (blocks < 1) {
+    bfly_plan_destroy(P);
+    return fail(BFLY_ERR_UNSUPPORTED, "recursive-step kernel cannot be resident with its shared memory");
+  }
+  P->level_grid = blocks * sms;
+  I.workspace_bytes = (int64_t)P->dbytes;
+  I.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = P;
+  return BFLY_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+bfly_status check_exec(bfly_plan_t P, const void *a, const void *b, int nrhs, int dtype) {
+  if (!P) return fail(BFLY_ERR_INVALID_ARG, "plan is NULL");
+  if (!P->dmem) return fail(BFLY_ERR_INVALID_ARG, "plan was created host-only");
+  if (!a || !b) return fail(BFLY_ERR_INVALID_ARG, "data pointer is NULL");
+  if (nrhs < 1 || nrhs > P->max_nrhs) return fail(BFLY_ERR_INVALID_ARG, "nrhs outside 1..max_nrhs");
+  if (dtype != BFLY_C64 && dtype != BFLY_C128) return fail(BFLY_ERR_INVALID_ARG, "unknown dtype");
+  return BFLY_OK;
+}
+
+bfly::PointArgs point_args(bfly_plan_t P, bool x_side, const void *vin, void *vout, int nrhs,
+                           bool io64, bool conj, int64_t tile_rhs) {
+  bfly::PointArgs a{};
+  a.vin = vin;
+  a.vout = vout;
+  a.nrhs = nrhs;
+  a.io64 = io64;
+  a.conj = conj;
+  a.tile_rhs = tile_rhs;
+  const HostTree &T = x_side ? P->TX : P->TK;
+  a.n_total = T.n;
+  a.nbox = T.nbox(P->L);
+  a.perm = x_side ? P->perm_x : P->perm_k;
+  a.leaf_start = x_side ? P->leaf_x : P->leaf_k;
+  a.point_leaf = x_side ? P->pleaf_x : P->pleaf_k;
+  a.W = x_side ? P->Wx : P->Wk;
+  return a;
+}
+
+bfly::LevelArgs level_args(bfly_plan_t P, int t, bool adjoint, int nrhs) {
+  const int L = P->L;
+  int PD = 1;
+  for (int d = 0; d < P->dim; ++d) PD *= P->p;
+  bfly::LevelArgs a{};
+  const int64_t nBt = P->TK.nbox(t), nBc = P->TK.nbox(t + 1);
+  void *bt = P->buf[t & 1], *bt1 = P->buf[(t + 1) & 1];
+  if (!adjoint) {
+    a.in = bt1;
+    a.out = bt;
+    a.in_row = nBc;
+    a.out_row = nBt;
+    a.in_rhs = P->pairs[t + 1] * PD;
+    a.out_rhs = P->pairs[t] * PD;
+    a.chunks = P->d_chf[t];
+    a.nchunks = (int)P->chf[t].size();
+    a.table = P->table;
+  } else {
+    a.in = bt;
+    a.out = bt1;
+    a.in_row = nBt;
+    a.out_row = nBc;
+    a.in_rhs = P->pairs[t] * PD;
+    a.out_rhs = P->pairs[t + 1] * PD;
+    a.chunks = P->d_cha[t];
+    a.nchunks = (int)P->cha[t].size();
+    a.table = P->tableH;
+  }
+  a.nrhs = nrhs;
+  a.nB = nBt;
+  a.xcs = P->xcs[L - t - 1];
+  a.xcode = P->xcode[L - t];
+  a.kcs = P->kcs[t];
+  a.kcode = P->kcode[t + 1];
+  a.tile_cap = P->tile_cap;
+  return a;
+}
+
+int plan_pd(bfly_plan_t P) {
+  int PD = 1;
+  for (int d = 0; d < P->dim; ++d) PD *= P->p;
+  return PD;
+}
+
+// Launches the sweep on stream s; when ev is non-null, records ev[i] before launch i and
+// ev[L+2] after the last one.
+bfly_status run(bfly_plan_t P, const void *in, void *out, int nrhs, int dtype, bool adjoint,
+                cudaStream_t s, cudaEvent_t const *ev = nullptr) {
+  const bool io64 = dtype == BFLY_C128;
+  const int L = P->L, PD = plan_pd(P);
+  int n = 0;
+  auto mark = [&]() -> cudaError_t {
+    cudaEvent_t e = ev ? ev[n++] : nullptr;
+    return e ? cudaEventRecord(e, s) : cudaSuccess;
+  };
+  if (!adjoint) {
+    // step 2: leaf charges (stage L) from the sources
+    BFLY_CUDA(mark());
+    BFLY_CUDA(P->ks->spread(point_args(P, false, in, P->buf[L & 1], nrhs, io64, false,
+                                       P->pairs[L] * PD), s));
+    // step 3: stages L-1 .. 0
+    for (int t = L - 1; t >= 0; --t) {
+      BFLY_CUDA(mark());
+      BFLY_CUDA(P->ks->level(level_args(P, t, false, nrhs), false, P->level_grid, P->level_smem, s));
+    }
+    // step 4: evaluate at the targets from stage 0
+    BFLY_CUDA(mark());
+    BFLY_CUDA(P->ks->interp(point_args(P, true, P->buf[0], out, nrhs, io64, false, P->pairs[0] * PD), s));
+  } else {
+    BFLY_CUDA(mark());
+    BFLY_CUDA(P->ks->spread(point_args(P, true, in, P->buf[0], nrhs, io64, true, P->pairs[0] * PD), s));
+    for (int t = 0; t < L; ++t) {
+      BFLY_CUDA(mark());
+      BFLY_CUDA(P->ks->level(level_args(P, t, true, nrhs), true, P->level_grid, P->level_smem, s));
+    }
+    BFLY_CUDA(mark());
+    BFLY_CUDA(P->ks->interp(point_args(P, false, P->buf[L & 1], out, nrhs, io64, true,
+                                       P->pairs[L] * PD), s));
+  }
+  BFLY_CUDA(mark());
+  return BFLY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bfly_status bfly_execute(bfly_plan_t plan, const void *f, void *u, int nrhs, int dtype, void *stream) {
+  g_err.clear();
+  bfly_status st = check_exec(plan, f, u, nrhs, dtype);
+  if (st != BFLY_OK) return st;
+  return run(plan, f, u, nrhs, dtype, false, reinterpret_cast<cudaStream_t>(stream));
+}
+
+bfly_status bfly_execute_adjoint(bfly_plan_t plan, const void *u, void *f, int nrhs, int dtype,
+                                 void *stream) {
+  g_err.clear();
+  bfly_status st = check_exec(plan, u, f, nrhs, dtype);
+  if (st != BFLY_OK) return st;
+  return run(plan, u, f, nrhs, dtype, true, reinterpret_cast<cudaStream_t>(stream));
+}
+
+bfly_status bfly_execute_host(bfly_plan_t plan, const void *in_host, void *out_host, int nrhs,
+                              int dtype, int adjoint, void *stream) {
+  g_err.clear();
+  bfly_status st = check_exec(plan, in_host, out_host, nrhs, dtype);
+  if (st != BFLY_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t eb = dtype == BFLY_C128 ? 16 : 8;
+  const int64_t nin = adjoint ? plan->nx : plan->nk, nout = adjoint ? plan->nk : plan->nx;
+  BFLY_CUDA(cudaMemcpyAsync(plan->stage_in, in_host, (size_t)nin * nrhs * eb, cudaMemcpyHostToDevice, s));
+  st = run(plan, plan->stage_in, plan->stage_out, nrhs, dtype, adjoint != 0, s);
+  if (st != BFLY_OK) return st;
+  BFLY_CUDA(cudaMemcpyAsync(out_host, plan->stage_out, (size_t)nout * nrhs * eb, cudaMemcpyDeviceToHost, s));
+  BFLY_CUDA(cudaStreamSynchronize(s));
+  return BFLY_OK;
+}
+
+bfly_status bfly_execute_events(bfly_plan_t plan, const void *in, void *out, int nrhs, int dtype,
+                                int adjoint, void *stream, void *const *events, int n_events) {
+  g_err.clear();
+  bfly_status st = check_exec(plan, in, out, nrhs, dtype);
+  if (st != BFLY_OK) return st;
+  if (!events || n_events != plan->L + 3) return fail(BFLY_ERR_INVALID_ARG, "events must hold L + 3 entries");
+  return run(plan, in, out, nrhs, dtype, adjoint != 0, reinterpret_cast<cudaStream_t>(stream),
+             reinterpret_cast<cudaEvent_t const *>(events));
+}
+
+bfly_status bfly_direct(bfly_plan_t plan, const void *in, void *out, int nrhs, int dtype, int adjoint,
+                        void *stream) {
+  g_err.clear();
+  bfly_status st = check_exec(plan, in, out, nrhs, dtype);
+  if (st != BFLY_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int prec = plan->prec == BFLY_PREC_FP64 ? 0 : 1;
+  if (!adjoint)
+    BFLY_CUDA(bfly::launch_direct(prec, plan->dim, plan->N, plan->nx, plan->xs, plan->nk, plan->ks_,
+                                  in, out, nrhs, dtype == BFLY_C128, +1.0, s));
+  else
+    BFLY_CUDA(bfly::launch_direct(prec, plan->dim, plan->N, plan->nk, plan->ks_, plan->nx, plan->xs,
+                                  in, out, nrhs, dtype == BFLY_C128, -1.0, s));
+  return BFLY_OK;
+}
+
+bfly_status bfly_plan_info(bfly_plan_t plan, bfly_plan_info_t *info) {
+  if (!plan || !info) return fail(BFLY_ERR_INVALID_ARG, "plan or info is NULL");
+  *info = plan->info;
+  return BFLY_OK;
+}
+
+bfly_status bfly_plan_stage(bfly_plan_t plan, int t, int64_t *nA, int64_t *nB) {
+  if (!plan || !nA || !nB) return fail(BFLY_ERR_INVALID_ARG, "NULL argument");
+  if (t < 0 || t > plan->L) return fail(BFLY_ERR_INVALID_ARG, "stage outside 0..L");
+  *nA = plan->TX.nbox(plan->L - t);
+  *nB = plan->TK.nbox(t);
+  return BFLY_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,36 @@
+// Launchers of the sm_103a kernels, one set per (precision, dimension, p).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bfly {
+
+struct KernelSet {
+  // recursive step at one stage; grid = persistent blocks, smem = dynamic bytes
+  cudaError_t (*level)(const LevelArgs &a, bool adjoint, int grid, size_t smem, cudaStream_t s);
+  // raises the dynamic shared memory limit to `smem` and returns resident blocks per SM
+  cudaError_t (*level_setup)(size_t smem, int *blocks_per_sm);
+  size_t (*level_smem)(int tile_cap);
+  size_t level_fixed_bytes, level_tile_bytes;
+  cudaError_t (*spread)(const PointArgs &a, cudaStream_t s);
+  cudaError_t (*interp)(const PointArgs &a, cudaStream_t s);
+};
+
+constexpr int kLevelThreads = 256;
+
+// prec: 0 = FP64, 1 = FP32.  Returns nullptr when (dim, p) has no kernels.
+const KernelSet *kernels_p3(int prec, int dim);
+const KernelSet *kernels_p5(int prec, int dim);
+const KernelSet *kernels_p7(int prec, int dim);
+const KernelSet *kernels_p9(int prec, int dim);
+
+cudaError_t launch_weights(int prec, int64_t n, int dim, int p, int kind, const double *off,
+                           const int32_t *point_leaf, const int32_t *leaf_idx,
+                           const double *inv_den, void *W, cudaStream_t s);
+cudaError_t launch_direct(int prec, int dim, double N, int64_t nt, const double *xt, int64_t ns,
+                          const double *xs, const void *in, void *out, int nrhs, bool io64,
+                          double sign, cudaStream_t s);
+
+}  // namespace bfly

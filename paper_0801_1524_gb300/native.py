@@ -1,0 +1,80 @@
+"""ctypes declarations of the C ABI in include/bfly.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbfly.so")
+
+BFLY_OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "UNSUPPORTED", 5: "TIMEOUT"}
+BFLY_C64, BFLY_C128 = 0, 1
+BFLY_PREC_FP64, BFLY_PREC_FP32 = 0, 1
+BFLY_FLAG_HOST_ONLY = 1
+
+# Every function the header declares, with (restype, argtypes).
+_vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("flags", ctypes.c_uint),
+                ("smem_kb", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("p", ctypes.c_int), ("L", ctypes.c_int),
+                ("prec", ctypes.c_int), ("N", ctypes.c_double), ("nx", ctypes.c_int64),
+                ("nk", ctypes.c_int64), ("total_pairs", ctypes.c_int64),
+                ("max_pairs", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("tiles_read_fwd", ctypes.c_int64), ("tiles_written_fwd", ctypes.c_int64),
+                ("jobs_fwd", ctypes.c_int64), ("chunks_fwd", ctypes.c_int64),
+                ("plan_seconds", ctypes.c_double)]
+
+
+SIGNATURES = {
+    "bfly_plan_create": (_i, [ctypes.POINTER(_vp), _i, _d, _i64, _vp, _i64, _vp, _i,
+                              ctypes.POINTER(Opts)]),
+    "bfly_plan_destroy": (None, [_vp]),
+    "bfly_execute": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
+    "bfly_execute_adjoint": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
+    "bfly_execute_host": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
+    "bfly_direct": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
+    "bfly_execute_events": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp, ctypes.POINTER(_vp), _i]),
+    "bfly_plan_info": (_i, [_vp, ctypes.POINTER(PlanInfo)]),
+    "bfly_plan_stage": (_i, [_vp, _i, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "bfly_last_error": (ctypes.c_char_p, []),
+    "bfly_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+class BflyError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(build_if_missing: bool = True):
+    """Loads libbfly.so (building it first if it is missing); raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if not build_if_missing:
+            raise RuntimeError(f"{LIB_PATH} is missing; run paper_0801_1524_gb300.build.build()")
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int, where: str):
+    if status != BFLY_OK:
+        raise BflyError(status, where, load().bfly_last_error().decode())

@@ -1,0 +1,187 @@
+"""Python binding of the butterfly: the same entry points as include/bfly.h, marshalling
+PyTorch tensors (device memory and streams) into the C ABI.  No arithmetic happens here;
+there is no CPU fallback: a missing or unloadable libbfly.so raises."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import native
+
+PRECISIONS = {"fp64": native.BFLY_PREC_FP64, "fp32": native.BFLY_PREC_FP32}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dtype_code(t):
+    torch = _torch()
+    if t.dtype == torch.complex64:
+        return native.BFLY_C64
+    if t.dtype == torch.complex128:
+        return native.BFLY_C128
+    raise TypeError(f"expected complex64 or complex128, got {t.dtype}")
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """Butterfly plan for targets x [nx, dim] and sources k [nk, dim] in [0, N]^dim.
+
+    forward(f):  u_i = sum_j exp(2 pi i x_i.k_j/N) f_j  (Sec. 2.2, approximate to eps(p))
+    adjoint(u):  the exact conjugate transpose of forward
+    direct(f):   eq. 1.1 summed term by term on the GPU
+    """
+
+    def __init__(self, x, k, N: float, p: int, precision: str = "fp32", max_nrhs: int = 1,
+                 host_only: bool = False, smem_kb: int = 0):
+        lib = native.load()
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        k = np.ascontiguousarray(k, dtype=np.float64)
+        if x.ndim != 2 or k.ndim != 2 or x.shape[1] != k.shape[1]:
+            raise ValueError("x and k must be [n, dim] arrays with the same dim")
+        if precision not in PRECISIONS:
+            raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+        self.dim = x.shape[1]
+        self.N = float(N)
+        self.p = int(p)
+        self.nx, self.nk = x.shape[0], k.shape[0]
+        self.precision = precision
+        self.max_nrhs = int(max_nrhs)
+        opts = native.Opts()
+        opts.prec = PRECISIONS[precision]
+        opts.max_nrhs = self.max_nrhs
+        opts.flags = native.BFLY_FLAG_HOST_ONLY if host_only else 0
+        opts.smem_kb = int(smem_kb)
+        h = ctypes.c_void_p()
+        self._lib = lib
+        self._h = None
+        native.check(lib.bfly_plan_create(ctypes.byref(h), self.dim, self.N, self.nx,
+                                          x.ctypes.data, self.nk, k.ctypes.data, self.p,
+                                          ctypes.byref(opts)), "bfly_plan_create")
+        self._h = h
+
+    # ---- lifetime
+    def close(self):
+        if self._h is not None:
+            self._lib.bfly_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- introspection
+    def info(self) -> dict:
+        inf = native.PlanInfo()
+        native.check(self._lib.bfly_plan_info(self._h, ctypes.byref(inf)), "bfly_plan_info")
+        return {name: getattr(inf, name) for name, _ in native.PlanInfo._fields_}
+
+    def stages(self) -> list:
+        """[(t, nA, nB)] for t = 0..L: stage t pairs nA T_X boxes with nB T_K boxes."""
+        out = []
+        L = self.info()["L"]
+        for t in range(L + 1):
+            a, b = ctypes.c_int64(), ctypes.c_int64()
+            native.check(self._lib.bfly_plan_stage(self._h, t, ctypes.byref(a), ctypes.byref(b)),
+                         "bfly_plan_stage")
+            out.append((t, a.value, b.value))
+        return out
+
+    # ---- execution on device tensors
+    def _prep(self, t, n, name):
+        torch = _torch()
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        squeeze = t.dim() == 1
+        t2 = t.reshape(1, -1) if squeeze else t
+        if t2.dim() != 2 or t2.shape[1] != n:
+            raise ValueError(f"{name} must be [{n}] or [nrhs, {n}]")
+        return t2.contiguous(), squeeze
+
+    def _run(self, fn, src, n_in, n_out, out, stream, name):
+        torch = _torch()
+        s, squeeze = self._prep(src, n_in, name)
+        if out is None:
+            out = torch.empty((s.shape[0], n_out), dtype=s.dtype, device=s.device)
+        o2 = out.reshape(s.shape[0], n_out)
+        if o2.dtype != s.dtype or not o2.is_contiguous():
+            raise ValueError("out must be contiguous with the input's dtype")
+        native.check(fn(self._h, ctypes.c_void_p(s.data_ptr()), ctypes.c_void_p(o2.data_ptr()),
+                        s.shape[0], _dtype_code(s), _stream_ptr(stream)), name)
+        return out.reshape(-1) if squeeze and out is not None and out.dim() == 2 else out
+
+    def forward(self, f, out=None, stream=None):
+        return self._run(self._lib.bfly_execute, f, self.nk, self.nx, out, stream, "bfly_execute")
+
+    def adjoint(self, u, out=None, stream=None):
+        return self._run(self._lib.bfly_execute_adjoint, u, self.nx, self.nk, out, stream,
+                         "bfly_execute_adjoint")
+
+    def direct(self, v, adjoint: bool = False, out=None, stream=None):
+        fn = lambda h, a, b, n, dt, st: self._lib.bfly_direct(h, a, b, n, dt, int(adjoint), st)
+        n_in, n_out = (self.nx, self.nk) if adjoint else (self.nk, self.nx)
+        return self._run(fn, v, n_in, n_out, out, stream, "bfly_direct")
+
+    def with_events(self, v, events, adjoint: bool = False, out=None, stream=None):
+        """bfly_execute_events: records the torch.cuda.Event list `events` (L + 3 of them,
+        already recorded once so that they exist) around every kernel launch."""
+        arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+        fn = lambda h, a, b, n, dt, st: self._lib.bfly_execute_events(h, a, b, n, dt, int(adjoint),
+                                                                      st, arr, len(events))
+        n_in, n_out = (self.nx, self.nk) if adjoint else (self.nk, self.nx)
+        return self._run(fn, v, n_in, n_out, out, stream, "bfly_execute_events")
+
+    # ---- execution on host buffers (copies inside the call)
+    def execute_host(self, v: np.ndarray, adjoint: bool = False, out: np.ndarray | None = None,
+                     stream=None) -> np.ndarray:
+        v2 = np.ascontiguousarray(np.atleast_2d(v))
+        n_in, n_out = (self.nx, self.nk) if adjoint else (self.nk, self.nx)
+        if v2.shape[1] != n_in or v2.dtype not in (np.complex64, np.complex128):
+            raise ValueError(f"input must be complex64/complex128 [nrhs, {n_in}]")
+        if out is None:
+            out = np.empty((v2.shape[0], n_out), dtype=v2.dtype)
+        code = native.BFLY_C128 if v2.dtype == np.complex128 else native.BFLY_C64
+        native.check(self._lib.bfly_execute_host(self._h, v2.ctypes.data, out.ctypes.data,
+                                                 v2.shape[0], code, int(adjoint),
+                                                 _stream_ptr(stream)), "bfly_execute_host")
+        return out[0] if np.ndim(v) == 1 else out
+
+
+def butterfly_fn():
+    """torch.autograd.Function u = B f with du/df handled by the adjoint sweep."""
+    torch = _torch()
+
+    class ButterflyFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, f, plan):
+            ctx.plan = plan
+            return plan.forward(f)
+
+        @staticmethod
+        def backward(ctx, g):
+            # PyTorch's complex gradient of a real loss is conj-Wirtinger: for u = B f
+            # the gradient with respect to f is B^H g, the adjoint sweep.
+            return ctx.plan.adjoint(g.contiguous()), None
+
+    return ButterflyFn
+
+
+def butterfly(f, plan):
+    """Differentiable forward transform: ButterflyFn.apply(f, plan)."""
+    return butterfly_fn().apply(f, plan)

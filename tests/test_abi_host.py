@@ -1,0 +1,97 @@
+"""CPU-only checks of the C ABI: the library builds, loads and exports every function
+include/bfly.h declares; argument validation; the host plan (trees and stage sizes)
+against the oracle's independent tree construction.  No kernel is launched."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle.butterfly as ob
+from paper_0801_1524_gb300 import native
+from paper_0801_1524_gb300 import workloads as w
+from paper_0801_1524_gb300.plan import Plan
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "bfly.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bfly_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_function():
+    lib = native.load()
+    names = header_functions()
+    assert "bfly_execute" in names and len(names) >= 9
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(native.SIGNATURES)
+    assert lib.bfly_version().decode().startswith("bfly")
+
+
+def _create(dim=2, N=16.0, x=None, k=None, p=5, flags=native.BFLY_FLAG_HOST_ONLY, prec=1):
+    lib = native.load()
+    if x is None:
+        x = w.random_points(10, 16.0, dim, 1)
+    if k is None:
+        k = w.random_points(10, 16.0, dim, 2)
+    x = np.ascontiguousarray(x, float)
+    k = np.ascontiguousarray(k, float)
+    h = ctypes.c_void_p()
+    o = native.Opts()
+    o.prec, o.max_nrhs, o.flags = prec, 1, flags
+    st = lib.bfly_plan_create(ctypes.byref(h), dim, float(N), x.shape[0], x.ctypes.data,
+                              k.shape[0], k.ctypes.data, p, ctypes.byref(o))
+    if st == 0:
+        lib.bfly_plan_destroy(h)
+    return st, lib.bfly_last_error().decode()
+
+
+@pytest.mark.parametrize("kw,status", [
+    (dict(dim=4), 1), (dict(dim=1), 1), (dict(p=2), 1), (dict(p=11), 1), (dict(p=4), 4),
+    (dict(N=24.0), 4), (dict(N=0.0), 1), (dict(N=float("nan")), 1),
+    (dict(x=np.array([[1.0, 17.0]])), 1), (dict(k=np.array([[-0.5, 1.0]])), 1),
+    (dict(k=np.array([[np.nan, 1.0]])), 1), (dict(prec=7), 1),
+])
+def test_invalid_arguments_are_reported(kw, status):
+    st, msg = _create(**kw)
+    assert st == status and msg
+
+
+def test_null_and_host_only_execution_rejected():
+    lib = native.load()
+    assert lib.bfly_plan_create(None, 2, 16.0, 1, None, 1, None, 5, None) == 1
+    P = Plan(w.random_points(5, 16.0, 2, 1), w.random_points(5, 16.0, 2, 2), 16.0, 5, host_only=True)
+    assert lib.bfly_execute(P._h, ctypes.c_void_p(8), ctypes.c_void_p(8), 1, 0, None) == 1
+    assert "host-only" in lib.bfly_last_error().decode()
+    assert lib.bfly_plan_stage(P._h, 99, ctypes.byref(ctypes.c_int64()), ctypes.byref(ctypes.c_int64())) == 1
+
+
+@pytest.mark.parametrize("dim,N,p,nx,nk,seed", [
+    (2, 1.0, 5, 7, 9, 1), (2, 64.0, 5, 300, 200, 2), (3, 16.0, 3, 400, 300, 3), (2, 2.0, 7, 20, 20, 4),
+])
+def test_stage_sizes_match_oracle_trees(dim, N, p, nx, nk, seed):
+    inst = w.small_random(dim, N, p, nx, nk, seed, edge_fraction=0.3)
+    P = Plan(inst.x, inst.k, N, p, host_only=True)
+    ref = ob.pair_counts(inst.x, inst.k, N)
+    got = {t: (a, b) for t, a, b in P.stages()}
+    assert got == ref
+    info = P.info()
+    assert info["total_pairs"] == sum(a * b for a, b in ref.values())
+    assert info["L"] == int(np.log2(N))
+
+
+def test_curve_workload_plan_counts():
+    inst = w.curve8192()
+    P = Plan(inst.x, inst.k, inst.N, inst.p, host_only=True)
+    info = P.info()
+    st = P.stages()
+    # Sec. 2.2: stage t pairs nA(L-t) x nK(t), O(N) per stage, L = log2 N stages.
+    assert info["L"] == 13 and len(st) == 14
+    assert st[0][2] == 1 and st[-1][1] == 1
+    assert all(a * b <= 12 * inst.N for _, a, b in st)
+    assert info["tiles_written_fwd"] == sum(a * b for t, a, b in st if t < 13)
+    assert info["plan_seconds"] < 5.0

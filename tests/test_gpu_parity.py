@@ -1,0 +1,170 @@
+"""Parity of the CUDA butterfly (through the C ABI) with the oracle.
+
+Tolerances (relative L2 over all outputs):
+  FP64 path vs the oracle's butterfly          1e-9   (the target for the FP64 path)
+  FP32 path vs the oracle's butterfly, p <= 7  1e-6   (the target for the FP32 path)
+  FP32 path, p = 9                             4e-6   (FP32 rounding through the sweep grows
+                                                       with the operator norm; see the
+                                                       precision notes of the design)
+  every path vs the direct sum (eq. 1.1)       2x the paper's largest eps_a for (dim, p)
+"""
+import numpy as np
+import pytest
+
+import oracle.butterfly as ob
+from conftest import paper_eps_bands, rel_l2
+from oracle.direct import direct, direct_adjoint
+from paper_0801_1524_gb300 import workloads as w
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BANDS = paper_eps_bands()
+TOL64 = 1e-9
+
+
+def tol32(p):
+    return 1e-6 if p <= 7 else 4e-6
+
+
+def _plan(inst, prec, nrhs=1):
+    from paper_0801_1524_gb300.plan import Plan
+    return Plan(inst.x, inst.k, inst.N, inst.p, precision=prec, max_nrhs=nrhs)
+
+
+def _gpu(a, dtype=torch.complex128):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _fwd(inst, f, prec, dtype=torch.complex128):
+    P = _plan(inst, prec, nrhs=1 if f.ndim == 1 else f.shape[0])
+    u = P.forward(_gpu(f, dtype))
+    torch.cuda.synchronize()
+    return u.cpu().numpy().astype(np.complex128)
+
+
+SMALL = [
+    # (dim, N, p, nx, nk, seed)
+    (2, 1.0, 5, 30, 25, 1),
+    (2, 2.0, 3, 40, 30, 2),
+    (2, 16.0, 5, 200, 150, 3),
+    (2, 64.0, 7, 500, 400, 4),
+    (2, 32.0, 9, 300, 300, 5),
+    (3, 4.0, 3, 200, 150, 6),
+    (3, 8.0, 5, 400, 300, 7),
+    (3, 4.0, 7, 150, 120, 8),
+]
+
+
+@pytest.mark.parametrize("dim,N,p,nx,nk,seed", SMALL)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_random_points_match_oracle(dim, N, p, nx, nk, seed, prec):
+    inst = w.small_random(dim, N, p, nx, nk, seed, edge_fraction=0.2)
+    f = inst.sources()[0]
+    ref = ob.butterfly(inst.x, inst.k, f, N, p)
+    got = _fwd(inst, f, prec)
+    assert rel_l2(got, ref) < (TOL64 if prec == "fp64" else tol32(p))
+
+
+@pytest.mark.parametrize("N,p", [(256.0, 5), (256.0, 7), (1024.0, 7), (512.0, 9)])
+def test_curves_match_oracle_and_band(N, p):
+    x = w.sample_curve(w.circle_curve(), N)
+    k = w.sample_curve(w.perturbed_ellipse_curve(), N)
+    inst = w.Instance("c", 2, N, p, x, k)
+    f = inst.sources()[0]
+    ref = ob.butterfly(x, k, f, N, p)
+    u64 = _fwd(inst, f, "fp64")
+    u32 = _fwd(inst, f, "fp32", torch.complex64)
+    assert rel_l2(u64, ref) < TOL64
+    assert rel_l2(u32, ref) < tol32(p)
+    assert rel_l2(u32, u64) < tol32(p)
+    eps = rel_l2(u64, direct(x, k, f, N))
+    assert eps < 2 * BANDS[(2, p)][1]
+
+
+def test_circle256_fp64_configuration():
+    inst = w.circle256()
+    f = inst.sources(dtype=np.complex128)[0]
+    ref = ob.butterfly(inst.x, inst.k, f, inst.N, inst.p)
+    u = _fwd(inst, f, "fp64")
+    assert rel_l2(u, ref) < TOL64
+    assert rel_l2(u, direct(inst.x, inst.k, f, inst.N)) < 2 * BANDS[(2, 5)][1]
+
+
+@pytest.mark.parametrize("p", [5, 7])
+def test_sphere_3d(p):
+    N = 16.0
+    x = w.fibonacci_sphere(N)
+    inst = w.Instance("s", 3, N, p, x, x.copy())
+    f = inst.sources()[0]
+    ref = ob.butterfly(x, x, f, N, p)
+    assert rel_l2(_fwd(inst, f, "fp64"), ref) < TOL64
+    assert rel_l2(_fwd(inst, f, "fp32", torch.complex64), ref) < tol32(p)
+
+
+def test_many_points_in_one_leaf_and_ragged():
+    # 700 sources in one unit leaf, 3 elsewhere; targets everywhere, some at N.
+    rng = np.random.default_rng(3)
+    N = 64.0
+    k = np.concatenate([rng.uniform(10.0, 11.0, (700, 2)), rng.uniform(0, N, (3, 2))])
+    x = w.random_points(257, N, 2, 4, edge_fraction=0.3)
+    inst = w.Instance("r", 2, N, 5, x, k)
+    f = inst.sources()[0]
+    ref = ob.butterfly(x, k, f, N, 5)
+    assert rel_l2(_fwd(inst, f, "fp64"), ref) < TOL64
+    assert rel_l2(_fwd(inst, f, "fp32"), ref) < tol32(5)
+
+
+def test_single_point_each_side():
+    inst = w.Instance("one", 2, 128.0, 7, np.array([[3.25, 100.5]]), np.array([[128.0, 0.0]]))
+    f = np.array([1.0 - 2.0j])
+    ref = ob.butterfly(inst.x, inst.k, f, inst.N, 7)
+    assert rel_l2(_fwd(inst, f, "fp64"), ref) < TOL64
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_multiple_rhs_and_io_dtypes(prec):
+    inst = w.small_random(2, 128.0, 5, 600, 500, 11)
+    f = inst.sources(nrhs=3)
+    ref = ob.butterfly(inst.x, inst.k, f, inst.N, 5)
+    tol = TOL64 if prec == "fp64" else tol32(5)
+    u128 = _fwd(inst, f, prec, torch.complex128)
+    u64 = _fwd(inst, f, prec, torch.complex64)
+    for r in range(3):
+        assert rel_l2(u128[r], ref[r]) < tol
+        assert rel_l2(u64[r], ref[r]) < (1e-6 if prec == "fp32" else 1e-6)
+    single = _fwd(inst, f[1], prec)
+    assert rel_l2(single, u128[1]) < 1e-14          # RHS are independent
+
+
+def test_deterministic():
+    inst = w.small_random(2, 256.0, 7, 2000, 2000, 12)
+    f = inst.sources()[0]
+    P = _plan(inst, "fp32")
+    a = P.forward(_gpu(f, torch.complex64))
+    b = P.forward(_gpu(f, torch.complex64))
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_direct_sum_on_gpu(prec):
+    inst = w.small_random(3, 32.0, 5, 700, 900, 13)
+    f = inst.sources(nrhs=2)
+    P = _plan(inst, prec, nrhs=2)
+    u = P.direct(_gpu(f)).cpu().numpy()
+    ref = direct(inst.x, inst.k, f, inst.N)
+    assert rel_l2(u, ref) < (1e-12 if prec == "fp64" else 2e-6)
+    uu = w.gaussian_sources(inst.x.shape[0], nrhs=2, seed=5)
+    fa = P.direct(_gpu(uu), adjoint=True).cpu().numpy()
+    assert rel_l2(fa, direct_adjoint(inst.x, inst.k, uu, inst.N)) < (1e-12 if prec == "fp64" else 2e-6)
+
+
+def test_execute_host_matches_device():
+    inst = w.small_random(2, 64.0, 7, 300, 250, 14)
+    f = inst.sources()[0].astype(np.complex64)
+    P = _plan(inst, "fp32")
+    dev = P.forward(_gpu(f, torch.complex64)).cpu().numpy()
+    host = P.execute_host(f)
+    assert np.array_equal(dev, host)
+    ua = P.execute_host(host, adjoint=True)
+    assert np.array_equal(ua, P.adjoint(_gpu(host, torch.complex64)).cpu().numpy())
