@@ -286,7 +286,7 @@ def main_bfly(args, rank, world, dist):
     # ---- roofline of the recursive step (the dominant kernel: L launches per step)
     d, p = inst.dim, inst.p
     PD = p ** d
-    flops = info["jobs_fwd"] * d * p ** (d + 1) * 8.0              # real flops, all stages
+    flops = info["flops_fwd"]          # real flops of the recursive step as executed, all stages
     bytes_ = (info["tiles_read_fwd"] + info["tiles_written_fwd"]) * PD * 8.0
     level_s = float(np.mean(level_ms)) * 1e-3
     per_launch_s = level_s / L
@@ -304,7 +304,7 @@ def main_bfly(args, rank, world, dist):
     main, alt = (roof_alu, roof_hbm) if roof_alu["frac"] >= roof_hbm["frac"] else (roof_hbm, roof_alu)
     main["traffic"] = traffic
     alt["traffic"] = traffic
-    main["kernel"] = "level_kernel<float,2,7,fwd> (recursive step, one launch per stage)"
+    main["kernel"] = "level_kernel<float,2,7> (recursive step, one launch per stage)"
     main["algorithmic_per_launch"] = {"flops": flops / L, "bytes": bytes_ / L}
     out["roofline_alt"] = alt
     kern_names = ["leaf"] + [f"level_t{t}" for t in range(L - 1, -1, -1)] + ["final"]

@@ -48,6 +48,10 @@ typedef enum { BFLY_PREC_FP64 = 0, BFLY_PREC_FP32 = 1 } bfly_precision;
 /* Build only the host plan: no device memory is touched, execution entry points return
  * BFLY_ERR_INVALID_ARG; bfly_plan_info and bfly_plan_stage still work.  */
 #define BFLY_FLAG_HOST_ONLY 1u
+/* Test hook for failure detection: every launch of the recursive step withholds the data
+ * of its first block of work and waits at most about a millisecond for it, so the bounded
+ * waits time out and set the device status word (results are then invalid). */
+#define BFLY_FLAG_TEST_STALL 2u
 
 typedef struct {
   int prec;          /* bfly_precision; default BFLY_PREC_FP32 */
@@ -67,8 +71,9 @@ typedef struct {
   int64_t workspace_bytes;      /* device bytes held by the plan */
   int64_t tiles_read_fwd;       /* recursive step: charge tiles read, forward, one RHS */
   int64_t tiles_written_fwd;    /* recursive step: charge tiles written, forward */
-  int64_t jobs_fwd;             /* (output box pair, child) contractions, forward */
+  int64_t jobs_fwd;             /* (output box pair, child) pairs of the recursive step */
   int64_t chunks_fwd;           /* blocks of work of the recursive step, all stages */
+  double flops_fwd;             /* real flops of the recursive step as executed, one RHS */
   double plan_seconds;          /* host wall time of bfly_plan_create */
 } bfly_plan_info_t;
 
@@ -149,6 +154,15 @@ bfly_status bfly_direct(bfly_plan_t plan, const void *in, void *out, int nrhs, i
 bfly_status bfly_execute_events(bfly_plan_t plan, const void *in, void *out, int nrhs,
                                 int dtype, int adjoint, void *stream, void *const *events,
                                 int n_events);
+
+/*
+ * bfly_device_status — waits for the device, then reads and clears the plan's device
+ * status word.  Kernels whose bounded waits gave up set bits in it (1: the copy engine
+ * side gave up waiting for a free buffer, 2: copies were still in flight at exit, 4: the
+ * compute side gave up waiting for data) and return early.  *flags (optional) receives
+ * the bits.  Returns BFLY_ERR_TIMEOUT when any bit was set, else BFLY_OK.
+ */
+bfly_status bfly_device_status(bfly_plan_t plan, int *flags);
 
 /* Sizes and counts of the plan (host data; no device access). */
 bfly_status bfly_plan_info(bfly_plan_t plan, bfly_plan_info_t *info);

@@ -12,7 +12,8 @@
 #include "kernels.hpp"
 #include "plan.hpp"
 
-using bfly::Chunk;
+using bfly::ChunkCaps;
+using bfly::StageProgram;
 using bfly::HostTree;
 using bfly::KernelSet;
 
@@ -53,10 +54,11 @@ struct bfly_plan_s {
   int device = -1;
   HostTree TX, TK;
   const KernelSet *ks = nullptr;
-  int tile_cap = 0, level_grid = 0;
+  ChunkCaps caps{};
+  int level_grid = 0, TS = 0;
   size_t level_smem = 0, elem_bytes = 0;
-  std::vector<std::vector<Chunk>> chf, cha;  // per stage t in [0, L-1]
-  std::vector<int64_t> pairs;                 // per stage t in [0, L]
+  std::vector<StageProgram> progF, progA;  // per stage t in [0, L-1]
+  std::vector<int64_t> pairs;              // per stage t in [0, L]
   // device memory: one allocation carved into the arrays below
   char *dmem = nullptr;
   size_t dbytes = 0;
@@ -64,9 +66,13 @@ struct bfly_plan_s {
   int32_t *pleaf_x = nullptr, *pleaf_k = nullptr, *lidx_x = nullptr;
   double *off_x = nullptr, *off_k = nullptr, *xs = nullptr, *ks_ = nullptr, *inv_den = nullptr;
   void *Wx = nullptr, *Wk = nullptr, *table = nullptr, *tableH = nullptr;
-  std::vector<int32_t *> xcs, kcs;       // level s in [0, L-1]
-  std::vector<uint32_t *> xcode, kcode;  // level s in [0, L] (0 unused)
-  std::vector<Chunk *> d_chf, d_cha;
+  struct DevProg {
+    bfly::ChunkDesc *chunks = nullptr;
+    unsigned char *blob = nullptr;
+    bfly::Run *runs = nullptr;
+  };
+  int *status = nullptr;  // device status word (bfly_device_status)
+  std::vector<DevProg> dF, dA;  // per stage t in [0, L-1]
   void *buf[2] = {nullptr, nullptr};
   void *stage_in = nullptr, *stage_out = nullptr;
   bfly_plan_info_t info{};
@@ -213,27 +219,49 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     P->device = dev;
     max_smem = (size_t)v;
   }
-  const size_t want = (size_t)(o.smem_kb > 0 ? o.smem_kb : 100) * 1024;
-  const int min_tiles = 2 << dim;  // the largest unit with a single output
-  auto cap_for = [&](size_t budget) -> int {
-    if (budget <= P->ks->level_fixed_bytes + 64) return 0;
-    size_t c = (budget - P->ks->level_fixed_bytes - 64) / (P->ks->level_tile_bytes + 2);
-    return (int)std::min<size_t>(c, 65535);
+  P->TS = P->ks->tile_stride;
+  // capacities: the largest chunk that fits the shared-memory budget of one block
+  const size_t want = (size_t)(o.smem_kb > 0 ? o.smem_kb : 55) * 1024;
+  auto caps_for = [&](size_t budget) {
+    ChunkCaps c{0, 0, 0};
+    for (int cap = 1024; cap >= 8; cap -= 8) {
+      c = ChunkCaps{cap, cap, cap, P->ks->meta_bytes(cap, cap, cap)};
+      if (P->ks->level_smem(c) <= budget) return c;
+    }
+    return ChunkCaps{0, 0, 0, 0};
   };
-  int cap = cap_for(std::min(want, max_smem));
-  if (cap < min_tiles) cap = cap_for(max_smem);
-  if (cap < min_tiles) {
+  ChunkCaps caps = caps_for(std::min(want, max_smem));
+  if (caps.cap0 == 0) caps = caps_for(max_smem);
+  if (caps.cap0 == 0) {
     delete P;
     return fail(BFLY_ERR_UNSUPPORTED, "charge tiles of this (dim, p, precision) do not fit in shared memory");
   }
-  P->tile_cap = cap;
-  P->level_smem = P->ks->level_smem(cap);
-  P->chf.resize(L);
-  P->cha.resize(L);
+  P->caps = caps;
+  P->level_smem = P->ks->level_smem(caps);
+  P->progF.resize(L);
+  P->progA.resize(L);
   for (int t = 0; t < L; ++t) {
-    P->chf[t] = bfly::make_chunks(P->TX.cs[L - t - 1], P->TK.cs[t], false, cap);
-    P->cha[t] = bfly::make_chunks(P->TX.cs[L - t - 1], P->TK.cs[t], true, cap);
-    I.chunks_fwd += (int64_t)P->chf[t].size();
+    const auto &csAp = P->TX.cs[L - t - 1], &xidx = P->TX.idx[L - t];
+    const auto &csB = P->TK.cs[t], &kidx = P->TK.idx[t + 1];
+    P->progF[t] = bfly::make_stage_program(dim, p, csAp, xidx, csB, kidx, false, caps);
+    P->progA[t] = bfly::make_stage_program(dim, p, csAp, xidx, csB, kidx, true, caps);
+    for (int dir = 0; dir < 2; ++dir) {
+      const int64_t tin = dir ? P->pairs[t] : P->pairs[t + 1], tout = dir ? P->pairs[t + 1] : P->pairs[t];
+      const std::string bad = bfly::validate_program(dir ? P->progA[t] : P->progF[t], dim, caps, tin, tout);
+      if (!bad.empty()) {
+        delete P;
+        return fail(BFLY_ERR_CUDA, "internal error in the stage program: " + bad);
+      }
+    }
+    I.chunks_fwd += (int64_t)P->progF[t].chunks.size();
+    int64_t srcs = 0;  // one task per (output tile of a pass, source)
+    for (const auto &cd : P->progF[t].chunks) {
+      const int32_t *hdr = reinterpret_cast<const int32_t *>(P->progF[t].blob.data() + cd.blob_off);
+      for (int k = 0; k < dim; ++k) srcs += hdr[2 * k] + hdr[2 * k + 1];  // tasks of pass k
+    }
+    double fib_p2 = 1.0;  // fibres x p^2 complex multiply-adds per source, 8 flops each
+    for (int d = 0; d < dim + 1; ++d) fib_p2 *= p;
+    I.flops_fwd += (double)srcs * fib_p2 * 8.0;
   }
   if (host_only) {
     I.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -242,23 +270,6 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   }
 
   // ---- device arrays
-  std::vector<uint32_t> empty_code;
-  std::vector<std::vector<uint32_t>> xcode(L + 1), kcode(L + 1);
-  for (int s = 1; s <= L; ++s) {
-    const int64_t nxs = P->TX.nbox(s), nks = P->TK.nbox(s);
-    xcode[s].resize(nxs);
-    kcode[s].resize(nks);
-    for (int64_t i = 0; i < nxs; ++i) {
-      uint32_t c = 0;
-      for (int d = 0; d < dim; ++d) c |= (uint32_t)(P->TX.idx[s][i * dim + d] % (2 * q)) << (8 * d);
-      xcode[s][i] = c;
-    }
-    for (int64_t i = 0; i < nks; ++i) {
-      uint32_t c = 0;
-      for (int d = 0; d < dim; ++d) c |= (uint32_t)(P->TK.idx[s][i * dim + d] & 1) << d;
-      kcode[s][i] = c;
-    }
-  }
   std::vector<double> inv_den(p);
   for (int m = 0; m < p; ++m) {
     double den = 1.0;
@@ -267,10 +278,21 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     inv_den[m] = 1.0 / den;
   }
   std::vector<double> tabF = bfly::transfer_table(p, false), tabH = bfly::transfer_table(p, true);
+  // FP32 operators for the recursive step: [op][l][m], m padded to an even count
   std::vector<float> tabF32, tabH32;
   if (o.prec == BFLY_PREC_FP32) {
-    tabF32.assign(tabF.begin(), tabF.end());
-    tabH32.assign(tabH.begin(), tabH.end());
+    const int pp = (p + 1) & ~1, nops = 4 * q;
+    tabF32.assign((size_t)nops * p * pp * 2, 0.0f);
+    tabH32.assign(tabF32.size(), 0.0f);
+    for (int op = 0; op < nops; ++op)
+      for (int m = 0; m < p; ++m)
+        for (int l = 0; l < p; ++l)
+          for (int c = 0; c < 2; ++c) {
+            const size_t from = (((size_t)op * p + m) * p + l) * 2 + c;
+            const size_t to = (((size_t)op * p + l) * pp + m) * 2 + c;
+            tabF32[to] = (float)tabF[from];
+            tabH32[to] = (float)tabH[from];
+          }
   }
   std::vector<double> xs(x, x + nx * dim), kv(k, k + nk * dim);
 
@@ -296,25 +318,20 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   }
   A.add(&P->Wx, (size_t)nx * dim * p * P->elem_bytes);
   A.add(&P->Wk, (size_t)nk * dim * p * P->elem_bytes);
-  P->xcs.assign(L, nullptr);
-  P->kcs.assign(L, nullptr);
-  P->xcode.assign(L + 1, nullptr);
-  P->kcode.assign(L + 1, nullptr);
-  P->d_chf.assign(L, nullptr);
-  P->d_cha.assign(L, nullptr);
-  for (int s = 0; s < L; ++s) {
-    A.add_vec(&P->xcs[s], P->TX.cs[s]);
-    A.add_vec(&P->kcs[s], P->TK.cs[s]);
-  }
-  for (int s = 1; s <= L; ++s) {
-    A.add_vec(&P->xcode[s], xcode[s]);
-    A.add_vec(&P->kcode[s], kcode[s]);
-  }
+  P->dF.resize(L);
+  P->dA.resize(L);
   for (int t = 0; t < L; ++t) {
-    A.add_vec(&P->d_chf[t], P->chf[t]);
-    A.add_vec(&P->d_cha[t], P->cha[t]);
+    for (int dir = 0; dir < 2; ++dir) {
+      StageProgram &pg = dir ? P->progA[t] : P->progF[t];
+      bfly_plan_s::DevProg &dp = dir ? P->dA[t] : P->dF[t];
+      A.add_vec(&dp.chunks, pg.chunks);
+      A.add_vec(&dp.blob, pg.blob);
+      A.add_vec(&dp.runs, pg.runs);
+    }
   }
-  const size_t buf_bytes = (size_t)maxp * PD * P->elem_bytes * o.max_nrhs;
+  static const int zero_status = 0;
+  A.add(reinterpret_cast<void **>(&P->status), sizeof(int), &zero_status);
+  const size_t buf_bytes = (size_t)maxp * P->TS * P->elem_bytes * o.max_nrhs;
   A.add(&P->buf[0], buf_bytes);
   A.add(&P->buf[1], buf_bytes);
   const size_t stage_bytes = (size_t)std::max(nx, nk) * 16 * o.max_nrhs;
@@ -354,8 +371,10 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     return fail(BFLY_ERR_CUDA, msg);
   }
   if (blocks < 1) {
+    const std::string msg = "recursive-step kernel cannot be resident with " +
+                            std::to_string(P->level_smem) + " bytes of shared memory";
     bfly_plan_destroy(P);
-    return fail(BFLY_ERR_UNSUPPORTED, "recursive-step kernel cannot be resident with its shared memory");
+    return fail(BFLY_ERR_UNSUPPORTED, msg);
   }
   P->level_grid = blocks * sms;
   I.workspace_bytes = (int64_t)P->dbytes;
@@ -386,6 +405,7 @@ bfly::PointArgs point_args(bfly_plan_t P, bool x_side, const void *vin, void *vo
   a.io64 = io64;
   a.conj = conj;
   a.tile_rhs = tile_rhs;
+  a.tile_stride = P->TS;
   const HostTree &T = x_side ? P->TX : P->TK;
   a.n_total = T.n;
   a.nbox = T.nbox(P->L);
@@ -397,55 +417,37 @@ bfly::PointArgs point_args(bfly_plan_t P, bool x_side, const void *vin, void *vo
 }
 
 bfly::LevelArgs level_args(bfly_plan_t P, int t, bool adjoint, int nrhs) {
-  const int L = P->L;
-  int PD = 1;
-  for (int d = 0; d < P->dim; ++d) PD *= P->p;
   bfly::LevelArgs a{};
-  const int64_t nBt = P->TK.nbox(t), nBc = P->TK.nbox(t + 1);
   void *bt = P->buf[t & 1], *bt1 = P->buf[(t + 1) & 1];
-  if (!adjoint) {
-    a.in = bt1;
-    a.out = bt;
-    a.in_row = nBc;
-    a.out_row = nBt;
-    a.in_rhs = P->pairs[t + 1] * PD;
-    a.out_rhs = P->pairs[t] * PD;
-    a.chunks = P->d_chf[t];
-    a.nchunks = (int)P->chf[t].size();
-    a.table = P->table;
-  } else {
-    a.in = bt;
-    a.out = bt1;
-    a.in_row = nBt;
-    a.out_row = nBc;
-    a.in_rhs = P->pairs[t] * PD;
-    a.out_rhs = P->pairs[t + 1] * PD;
-    a.chunks = P->d_cha[t];
-    a.nchunks = (int)P->cha[t].size();
-    a.table = P->tableH;
-  }
+  const StageProgram &pg = adjoint ? P->progA[t] : P->progF[t];
+  const bfly_plan_s::DevProg &dp = adjoint ? P->dA[t] : P->dF[t];
+  a.in = adjoint ? bt : bt1;
+  a.out = adjoint ? bt1 : bt;
+  a.in_rhs = (adjoint ? P->pairs[t] : P->pairs[t + 1]) * P->TS;
+  a.out_rhs = (adjoint ? P->pairs[t + 1] : P->pairs[t]) * P->TS;
   a.nrhs = nrhs;
-  a.nB = nBt;
-  a.xcs = P->xcs[L - t - 1];
-  a.xcode = P->xcode[L - t];
-  a.kcs = P->kcs[t];
-  a.kcode = P->kcode[t + 1];
-  a.tile_cap = P->tile_cap;
+  a.chunks = dp.chunks;
+  a.nchunks = (int)pg.chunks.size();
+  a.blob = dp.blob;
+  a.runs = dp.runs;
+  a.table = adjoint ? P->tableH : P->table;
+  a.cap0 = P->caps.cap0;
+  a.cap1 = P->caps.cap1;
+  a.meta_bytes = P->caps.meta_bytes;
+  const bool stall = (P->flags & BFLY_FLAG_TEST_STALL) != 0;
+  a.wait_limit = stall ? 2000000LL : 2000000000LL;  // ~1 ms / ~1 s of SM clock
+  a.status = P->status;
+  a.inject_stall = stall ? 1 : 0;
   return a;
 }
 
-int plan_pd(bfly_plan_t P) {
-  int PD = 1;
-  for (int d = 0; d < P->dim; ++d) PD *= P->p;
-  return PD;
-}
 
 // Launches the sweep on stream s; when ev is non-null, records ev[i] before launch i and
 // ev[L+2] after the last one.
 bfly_status run(bfly_plan_t P, const void *in, void *out, int nrhs, int dtype, bool adjoint,
                 cudaStream_t s, cudaEvent_t const *ev = nullptr) {
   const bool io64 = dtype == BFLY_C128;
-  const int L = P->L, PD = plan_pd(P);
+  const int L = P->L, PD = P->TS;
   int n = 0;
   auto mark = [&]() -> cudaError_t {
     cudaEvent_t e = ev ? ev[n++] : nullptr;
@@ -537,6 +539,18 @@ bfly_status bfly_direct(bfly_plan_t plan, const void *in, void *out, int nrhs, i
   else
     BFLY_CUDA(bfly::launch_direct(prec, plan->dim, plan->N, plan->nk, plan->ks_, plan->nx, plan->xs,
                                   in, out, nrhs, dtype == BFLY_C128, -1.0, s));
+  return BFLY_OK;
+}
+
+bfly_status bfly_device_status(bfly_plan_t plan, int *flags) {
+  g_err.clear();
+  if (!plan || !plan->status) return fail(BFLY_ERR_INVALID_ARG, "plan is NULL or host-only");
+  int v = 0;
+  BFLY_CUDA(cudaDeviceSynchronize());
+  BFLY_CUDA(cudaMemcpy(&v, plan->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v) BFLY_CUDA(cudaMemset(plan->status, 0, sizeof(int)));
+  if (flags) *flags = v;
+  if (v) return fail(BFLY_ERR_TIMEOUT, "a bounded device-side wait gave up (status bits " + std::to_string(v) + ")");
   return BFLY_OK;
 }
 

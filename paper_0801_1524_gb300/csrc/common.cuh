@@ -1,5 +1,5 @@
-// Device helpers shared by the butterfly kernels: complex arithmetic on float2/double2,
-// a block-wide exclusive scan, and the argument blocks of every kernel.
+// Device helpers shared by the butterfly kernels: complex arithmetic on float2/double2
+// and the argument blocks of every kernel.
 #pragma once
 
 #include <cstdint>
@@ -74,58 +74,25 @@ __device__ __forceinline__ void store_io(void *p, int64_t i, C v, bool io64) {
   }
 }
 
-// Exclusive scan of one int per thread over a block of NT threads (NT a multiple of 32,
-// at most 1024).  `tmp` holds NT/32 ints of shared memory.  Returns the exclusive
-// prefix; *total receives the block sum.  Contains __syncthreads().
-template <int NT>
-__device__ __forceinline__ int block_exclusive_scan(int v, int *tmp, int *total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  if (lane == 31) tmp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    int w = lane < NT / 32 ? tmp[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += y;
-    }
-    if (lane < NT / 32) tmp[lane] = w;  // inclusive warp totals
-  }
-  __syncthreads();
-  const int base = warp > 0 ? tmp[warp - 1] : 0;
-  *total = tmp[NT / 32 - 1];
-  __syncthreads();
-  return base + incl - v;
-}
-
 // ---------------------------------------------------------------------------------------
-// Recursive step (Sec. 2.2 step 3) at one stage t.
-//   forward : in = stage t+1 charges [rhs][nAp][in_row][P^D], out = stage t charges
-//             [rhs][nA][out_row][P^D]; unit (A', B) reads f^{A'Bc} for the children Bc
-//             of B and writes f^{AB} for the children A of A'.
-//   adjoint : in = stage t, out = stage t+1; the unit reads the tiles of the children A
-//             of A' and writes the tiles of the children Bc of B.
+// Recursive step (Sec. 2.2 step 3) at one stage t, as a compiled chunk program (plan.hpp).
+//   forward : in = stage t+1 charges, out = stage t charges;
+//   adjoint : in = stage t, out = stage t+1.
+// A stage buffer holds [rhs][tile][TS] complex values, TS = tile stride (level.cuh).
 struct LevelArgs {
   const void *in;
   void *out;
-  int64_t in_row, out_row;    // tiles per row (number of B boxes) of in and out
-  int64_t in_rhs, out_rhs;    // elements between right-hand sides
+  int64_t in_rhs, out_rhs;      // elements between right-hand sides
   int nrhs;
-  int64_t nB;                 // B boxes at level t (units = nAp * nB)
-  const int32_t *xcs;         // [nAp+1] children of A' (T_X level L-t-1 -> L-t)
-  const uint32_t *xcode;      // [nA] alpha_d = a_d mod 2q, 8 bits per axis
-  const int32_t *kcs;         // [nB+1] children of B (T_K level t -> t+1)
-  const uint32_t *kcode;      // [nBc] delta_d = b_d & 1, 1 bit per axis
-  const Chunk *chunks;
+  const ChunkDesc *chunks;
   int nchunks;
-  const void *table;          // [4q][P][P] complex operators (conjugate-transposed: adjoint)
-  int tile_cap;               // charge tiles of shared memory per block
+  const unsigned char *blob;    // per-chunk metadata blobs (plan.hpp)
+  const Run *runs;
+  const void *table;            // [4q][P][P] complex operators (conjugate-transposed: adjoint)
+  int cap0, cap1, meta_bytes;   // shared-memory capacities the program was compiled for
+  long long wait_limit;         // clock cycles before a wait gives up
+  int *status;                  // device status word: bits set on a timeout
+  int inject_stall;             // test hook: withhold the copies of the first chunk
 };
 
 // Steps 2 and 4 and their adjoints: per-point weights against one tile per leaf.
@@ -139,6 +106,7 @@ struct PointArgs {
   int64_t n_total;            // points in caller order (stride between rhs of caller data)
   int64_t nbox;               // leaves
   int64_t tile_rhs;           // elements between rhs of the tile buffer
+  int tile_stride;            // elements between consecutive tiles
   int nrhs;
   bool io64;                  // caller data is complex128
   bool conj;                  // use conj(W)

@@ -12,13 +12,14 @@ struct KernelSet {
   cudaError_t (*level)(const LevelArgs &a, bool adjoint, int grid, size_t smem, cudaStream_t s);
   // raises the dynamic shared memory limit to `smem` and returns resident blocks per SM
   cudaError_t (*level_setup)(size_t smem, int *blocks_per_sm);
-  size_t (*level_smem)(int tile_cap);
-  size_t level_fixed_bytes, level_tile_bytes;
+  size_t (*level_smem)(const ChunkCaps &caps);
+  int (*meta_bytes)(int cap0, int cap1, int max_out);
+  size_t level_table_bytes, level_tile_bytes;
+  int tile_stride;  // complex elements per stored charge tile
   cudaError_t (*spread)(const PointArgs &a, cudaStream_t s);
   cudaError_t (*interp)(const PointArgs &a, cudaStream_t s);
 };
 
-constexpr int kLevelThreads = 256;
 
 // prec: 0 = FP64, 1 = FP32.  Returns nullptr when (dim, p) has no kernels.
 const KernelSet *kernels_p3(int prec, int dim);

@@ -9,27 +9,21 @@ namespace {
 
 template <typename R, int D, int P>
 struct Impl {
-  using S = LevelSmem<R, D, P>;
+  using S = LevelShape<R, D, P>;
   static cudaError_t level(const LevelArgs &a, bool adjoint, int grid, size_t smem, cudaStream_t s) {
+    (void)adjoint;  // the adjoint differs only in its program and operator table
     if (a.nchunks <= 0) return cudaSuccess;
-    if (adjoint)
-      level_kernel<R, D, P, true, kLevelThreads><<<grid, kLevelThreads, smem, s>>>(a);
-    else
-      level_kernel<R, D, P, false, kLevelThreads><<<grid, kLevelThreads, smem, s>>>(a);
+    level_kernel<R, D, P><<<grid, kLevelThreads, smem, s>>>(a);
     return cudaGetLastError();
   }
   static cudaError_t level_setup(size_t smem, int *blocks) {
-    cudaError_t e;
-    e = cudaFuncSetAttribute(level_kernel<R, D, P, false, kLevelThreads>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(level_kernel<R, D, P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(level_kernel<R, D, P, true, kLevelThreads>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        blocks, level_kernel<R, D, P, false, kLevelThreads>, kLevelThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, level_kernel<R, D, P>, kLevelThreads, smem);
   }
-  static size_t level_smem(int tile_cap) { return S::bytes(tile_cap); }
+  static size_t level_smem(const ChunkCaps &c) { return S::bytes(c); }
+  static int meta_bytes(int cap0, int cap1, int max_out) { return S::meta_bytes(cap0, cap1, max_out); }
   static cudaError_t spread(const PointArgs &a, cudaStream_t s) {
     constexpr int PD = ipow(P, D);
     const int64_t work = a.nbox * PD;
@@ -45,8 +39,9 @@ struct Impl {
     return cudaGetLastError();
   }
   static const KernelSet *get() {
-    static const KernelSet ks = {&level, &level_setup, &level_smem, S::fixed_bytes, S::tile_bytes,
-                                 &spread, &interp};
+    static const KernelSet ks = {&level,         &level_setup,  &level_smem, &meta_bytes,
+                                 S::table_bytes, S::tile_bytes, S::TS,      &spread,
+                                 &interp};
     return &ks;
   }
 };

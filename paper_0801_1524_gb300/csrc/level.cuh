@@ -2,207 +2,360 @@
 //
 // For every pair (A, B) at stage t the charges are
 //     f^{AB} = sum_{c in children(B)} ( (x)_d T^{(alpha_d(A), delta_d(c))} ) f^{A' Bc}
-// with A' the parent of A and T the per-axis transfer operators (plan.cpp).  Work is
-// grouped by unit (A', B): its inputs f^{A'Bc} are read once and shared by the outputs
-// f^{AB} of every child A of A' (forward); the adjoint reads f^{AB} of the children A
-// and writes f^{A'Bc} of the children Bc, with conjugate-transposed operators.
+// with A' the parent of A and T the per-axis transfer operators (plan.cpp).  The host
+// compiles every stage into chunks of units (A', B) with one item list per axis: pass k
+// applies the operator of axis k to at most two source tiles and sums them (the sources
+// agree on every bit still to be applied; sum factorisation):
+//   inputs --pass 0--> scratch --pass 1 (3D)--> input slot --last pass--> global.
+// The adjoint sweep runs the same kernel on the adjoint program with the
+// conjugate-transposed operators.
 //
-// A persistent block walks over chunks of consecutive units (planned on the host so
-// that the chunk's tiles fit in shared memory), stages the input tiles in shared
-// memory, applies the operator of axis 0..D-2 fibre by fibre into one scratch tile per
-// (output, input) job, and applies the last axis while summing the jobs of an output,
-// writing the result straight to global memory.
+// A persistent block is warp-specialised.  One producer warp walks over the block's
+// chunks (times right-hand sides).  For chunk i in slot s = i mod 2 it first writes back
+// the outputs of chunk i-2, staged by the consumers in slot s (bulk stores of contiguous
+// output runs, cp.async.bulk shared -> global), waits until those stores have read the
+// slot, then copies chunk i's metadata blob and input tiles (runs of consecutive 16-byte
+// aligned tiles) into the slot with bulk copies completing on the slot's "full" mbarrier.
+// The consumer warps wait on "full" and run the passes.  A pass is two phases of tasks
+// (first sources: store; second sources: add), each grouped by operator; a group's
+// fibres are taken 32 at a time ("steps", one fibre per lane), a warp takes a contiguous
+// range of steps, loads each group's operator once into registers (the same operator in
+// every lane, so no divergence) and streams its fibres through it: P loads, P^2 complex
+// multiply-adds and P stores per fibre.  The last pass stages its tiles in the slot; the consumers then signal
+// the slot's "staged" mbarrier and go on with the other slot, so that the write-back and
+// the next copies overlap their compute.  Every mbarrier wait gives up after a clock
+// budget, sets the status word and leaves the loop together with its peers; the producer
+// then waits (again bounded) for the copies it issued before the block exits.
 #pragma once
 
 #include "common.cuh"
 
 namespace bfly {
 
+template <typename R>
+__host__ __device__ constexpr int tile_stride(int pd) {
+  // complex elements per stored tile: a multiple of 16 bytes
+  return sizeof(R) == 4 ? (pd + 1) & ~1 : pd;
+}
+
+constexpr int kConsumerWarps = 7;  // + 1 producer: 8 warps, two per SM sub-partition
+constexpr int kLevelThreads = (kConsumerWarps + 1) * 32;
+constexpr int kLevelBlocksPerSm = 4;
+
 template <typename R, int D, int P>
-struct LevelSmem {
+struct LevelShape {
   using C = typename Cx<R>::T;
   static constexpr int Q = P - 1;
   static constexpr int NOPS = 4 * Q;
   static constexpr int PD = ipow(P, D);
-  static constexpr size_t table_bytes = (size_t)NOPS * P * P * sizeof(C);
-  // per unit: iAp, iB, a0, c0, olo, nin, nout
-  static constexpr size_t unit_bytes = (size_t)kMaxUnits * 7 * sizeof(int);
-  // per input: global tile (int64) + code ; per output: global tile, code, job base,
-  // input base, input count
-  static constexpr size_t in_bytes = (size_t)kMaxIn * (sizeof(int64_t) + sizeof(uint32_t));
-  static constexpr size_t out_bytes = (size_t)kMaxOut * (sizeof(int64_t) + 4 * sizeof(int));
-  static constexpr size_t fixed_bytes = table_bytes + unit_bytes + in_bytes + out_bytes + 64 * sizeof(int);
-  static constexpr size_t tile_bytes = (size_t)PD * sizeof(C);
-  // per tile of capacity: the tile and one job->output map entry
-  static size_t bytes(int tile_cap) {
-    size_t b = fixed_bytes + (size_t)tile_cap * sizeof(uint16_t);
-    b = (b + 15) & ~(size_t)15;
-    return b + (size_t)tile_cap * tile_bytes;
+  static constexpr int TS = tile_stride<R>(PD);
+  static constexpr int FIB = PD / P;  // fibres of one tile along one axis
+  // FP32 operators are stored transposed, [op][l][m] with m padded to PP entries, so that
+  // one 16-byte load reads T[m][l] and T[m+1][l]; FP64 operators as [op][m][l]
+  static constexpr int PP = sizeof(R) == 4 ? (P + 1) & ~1 : P;
+  static constexpr int OPS = sizeof(R) == 4 ? P * PP : P * P;  // elements per operator
+  static constexpr size_t table_bytes = (size_t)NOPS * OPS * sizeof(C);
+  static constexpr size_t tile_bytes = (size_t)TS * sizeof(C);
+  static int meta_bytes(int cap0, int cap1, int max_out) {
+    // at most two tasks and two operator groups per item, one run per output
+    const int items = cap1 + (D == 3 ? cap0 : 0) + max_out;
+    return (64 + 32 * items + 8 * max_out + 15) & ~15;
+  }
+  // table | 4 mbarriers | 2 metadata slots | 2 input buffers | scratch (2 in 3D, where
+  // the last pass stages its outputs there)
+  static constexpr int NSCR = D == 3 ? 2 : 1;
+  static size_t bytes(const ChunkCaps &c) {
+    size_t b = (table_bytes + 15) & ~(size_t)15;
+    b += 64;
+    b += 2 * (size_t)c.meta_bytes;
+    return b + (2 * (size_t)c.cap0 + NSCR * (size_t)c.cap1) * tile_bytes;
   }
 };
 
-template <typename R, int D, int P, bool ADJ, int NT>
-__global__ void __launch_bounds__(NT) level_kernel(const LevelArgs a) {
+// ---- PTX wrappers: mbarrier and 1D bulk copies (sm_90+)
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Waits for the phase of `bar` with the given parity to complete; false after `limit`
+// clock cycles.  Between polls the warp sleeps (growing to `max_sleep_ns`), so that a
+// waiting warp leaves the issue slots of its SM sub-partition to the computing warps.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long limit,
+                                          unsigned max_sleep_ns = 256) {
+  const unsigned a = smem_addr(bar);
+  const long long t0 = clock64();
+  unsigned ns = 8;
+  for (;;) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > limit) return false;
+    __nanosleep(ns);
+    if (ns < max_sleep_ns) ns *= 2;
+  }
+}
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst),
+               "r"(smem_addr(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void consumer_sync() {
+  asm volatile("bar.sync 1, %0;\n" ::"r"(kConsumerWarps * 32) : "memory");
+}
+// Barrier over the consumer warps that also returns whether any of them passed `v`.
+__device__ __forceinline__ bool consumer_any(bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 2, %2, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((unsigned)v), "r"(kConsumerWarps * 32)
+      : "memory");
+  return r != 0;
+}
+
+// One phase of pass K, warp `warp` of the consumers: for its steps (32 fibres of one
+// operator group, one per lane), y = T^{op} x along axis K, stored to (add = false) or
+// added to (add = true) the destination tile.
+template <typename R, int D, int P, int K>
+__device__ __forceinline__ void run_phase(const Task *tasks, const Group *groups, int ng,
+                                          const typename Cx<R>::T *src, typename Cx<R>::T *dst,
+                                          bool add, const typename Cx<R>::T *table, int warp,
+                                          int lane) {
   using C = typename Cx<R>::T;
-  using S = LevelSmem<R, D, P>;
-  constexpr int PD = S::PD, FIB = PD / P, NOPS = S::NOPS;
-  extern __shared__ __align__(16) unsigned char smem[];
+  using S = LevelShape<R, D, P>;
+  constexpr int FIB = S::FIB, TS = S::TS;
+  constexpr int SK = ipow(P, D - 1 - K);  // element stride of axis K
+  if (ng <= 0) return;
+  const Group last = groups[ng - 1];
+  const int nsteps = last.step_begin + (last.n_tasks * FIB + 31) / 32;
+  const int per = (nsteps + kConsumerWarps - 1) / kConsumerWarps;
+  const int s0 = warp * per, s1 = min(nsteps, s0 + per);
+  if (s0 >= s1) return;
+  int g = 0;
+  while (g + 1 < ng && groups[g + 1].step_begin <= s0) ++g;
+#pragma unroll 1
+  for (; g < ng; ++g) {
+    const Group gr = groups[g];
+    if (gr.step_begin >= s1) break;
+    const int nfib = gr.n_tasks * FIB;
+    const int a = max(s0, (int)gr.step_begin), b = min(s1, gr.step_begin + (nfib + 31) / 32);
+    // the group's operator, the same in every lane: its reads are broadcasts
+    const C *Tg = table + (size_t)gr.op * S::OPS;
+#pragma unroll 1
+    for (int st = a; st < b; ++st) {
+      const int fl = (st - gr.step_begin) * 32 + lane;
+      if (fl >= nfib) continue;
+      const int ti = fl / FIB, f = fl - ti * FIB;
+      const Task tk = tasks[gr.task_begin + ti];
+      const int base = (f / SK) * SK * P + (f % SK);
+      const C *X = src + (size_t)tk.src * TS + base;
+      C x[P];
+#pragma unroll
+      for (int l = 0; l < P; ++l) x[l] = X[l * SK];
+      C *Y = dst + (size_t)tk.dst * TS + base;
+      C y[P];
+#pragma unroll
+      for (int m = 0; m < P; ++m) y[m] = add ? Y[m * SK] : cmk((R)0, (R)0);
+      // l outer, m inner: 2P independent multiply-add chains in flight
+#pragma unroll
+      for (int l = 0; l < P; ++l) {
+        if (sizeof(R) == 4) {
+          const float4 *Tl = reinterpret_cast<const float4 *>(Tg + l * S::PP);
+#pragma unroll
+          for (int m = 0; m < P; m += 2) {
+            const float4 t2 = Tl[m / 2];
+            y[m] = cfma(cmk((R)t2.x, (R)t2.y), x[l], y[m]);
+            if (m + 1 < P) y[m + 1] = cfma(cmk((R)t2.z, (R)t2.w), x[l], y[m + 1]);
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < P; ++m) y[m] = cfma(Tg[m * P + l], x[l], y[m]);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < P; ++m) Y[m * SK] = y[m];
+    }
+  }
+}
+
+// Pass K: phase 0 (first sources, store), then phase 1 (second sources, add).
+template <typename R, int D, int P, int K>
+__device__ __forceinline__ void run_pass(const Task *tasks, const int32_t *hdr, const Group *groups,
+                                         const typename Cx<R>::T *src, typename Cx<R>::T *dst,
+                                         const typename Cx<R>::T *table, int warp, int lane) {
+  const int n0 = hdr[2 * K], g0 = hdr[6 + 2 * K], g1 = hdr[6 + 2 * K + 1];
+  run_phase<R, D, P, K>(tasks, groups, g0, src, dst, false, table, warp, lane);
+  consumer_sync();
+  if (g1 > 0) run_phase<R, D, P, K>(tasks + n0, groups + g0, g1, src, dst, true, table, warp, lane);
+  consumer_sync();
+}
+
+template <typename R, int D, int P>
+__global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel(const LevelArgs a) {
+  using C = typename Cx<R>::T;
+  using S = LevelShape<R, D, P>;
+  constexpr int TS = S::TS, NOPS = S::NOPS;
+  extern __shared__ __align__(128) unsigned char smem[];
   unsigned char *ptr = smem;
   C *s_table = reinterpret_cast<C *>(ptr);
-  ptr += S::table_bytes;
-  int *s_u = reinterpret_cast<int *>(ptr);  // [7][kMaxUnits]
-  ptr += S::unit_bytes;
-  int64_t *s_in_g = reinterpret_cast<int64_t *>(ptr);
-  uint32_t *s_in_code = reinterpret_cast<uint32_t *>(s_in_g + kMaxIn);
-  ptr += S::in_bytes;
-  int64_t *s_out_g = reinterpret_cast<int64_t *>(ptr);
-  uint32_t *s_out_code = reinterpret_cast<uint32_t *>(s_out_g + kMaxOut);
-  int *s_out_jb = reinterpret_cast<int *>(s_out_code + kMaxOut);
-  int *s_out_inb = s_out_jb + kMaxOut;
-  int *s_out_nin = s_out_inb + kMaxOut;
-  ptr += S::out_bytes;
-  int *s_tmp = reinterpret_cast<int *>(ptr);  // scan scratch + totals
-  ptr += 64 * sizeof(int);
-  uint16_t *s_job_out = reinterpret_cast<uint16_t *>(ptr);
-  ptr += (size_t)a.tile_cap * sizeof(uint16_t);
-  ptr = smem + ((size_t)(ptr - smem + 15) & ~(size_t)15);
-  C *s_tiles = reinterpret_cast<C *>(ptr);
+  ptr += (S::table_bytes + 15) & ~(size_t)15;
+  uint64_t *full = reinterpret_cast<uint64_t *>(ptr);  // full[2], staged[2]
+  uint64_t *staged = full + 2;
+  ptr += 64;
+  unsigned char *meta0 = ptr;  // slot s at meta0 + s * meta_bytes
+  ptr += 2 * (size_t)a.meta_bytes;
+  // slot s: input buffer (cap0 tiles) at slot0 + s * cap0 * TS; scratch s (cap1 tiles)
+  // at scr0 + (s mod NSCR) * cap1 * TS
+  C *slot0 = reinterpret_cast<C *>(ptr);
+  C *scr0 = slot0 + 2 * (size_t)a.cap0 * TS;
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const C *table = reinterpret_cast<const C *>(a.table);
-  for (int e = tid; e < NOPS * P * P; e += NT) s_table[e] = table[e];
+  for (int e = tid; e < NOPS * S::OPS; e += kLevelThreads) s_table[e] = table[e];
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&staged[0], 1);
+    mbar_init(&staged[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
 
-  int *u_iAp = s_u, *u_iB = s_u + kMaxUnits, *u_a0 = s_u + 2 * kMaxUnits, *u_c0 = s_u + 3 * kMaxUnits;
-  int *u_olo = s_u + 4 * kMaxUnits, *u_nin = s_u + 5 * kMaxUnits, *u_nout = s_u + 6 * kMaxUnits;
+  const int my_chunks = blockIdx.x < a.nchunks ? (a.nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int n_work = my_chunks * a.nrhs;
+  const unsigned char *gin = reinterpret_cast<const unsigned char *>(a.in);
+  unsigned char *gout = reinterpret_cast<unsigned char *>(a.out);
 
-  const C *gin = reinterpret_cast<const C *>(a.in);
-  C *gout = reinterpret_cast<C *>(a.out);
-
-  for (int ch = blockIdx.x; ch < a.nchunks; ch += gridDim.x) {
-    const Chunk c = a.chunks[ch];
-    // ---- 1. the chunk's units and their input/output/job counts
-    int nin = 0, nout = 0, njob = 0;
-    if (tid < c.nu) {
-      const int64_t u = c.u0 + tid;
-      const int iAp = (int)(u / a.nB), iB = (int)(u % a.nB);
-      const int a0 = a.xcs[iAp], a1 = a.xcs[iAp + 1];
-      const int c0 = a.kcs[iB], c1 = a.kcs[iB + 1];
-      const int na = a1 - a0, nc = c1 - c0;
-      nin = ADJ ? na : nc;
-      const int full = ADJ ? nc : na;
-      const int olo = c.nu == 1 ? (int)c.o_lo : 0;
-      const int ohi = c.nu == 1 ? min((int)c.o_hi, full) : full;
-      nout = ohi - olo;
-      njob = nin * nout;
-      u_iAp[tid] = iAp;
-      u_iB[tid] = iB;
-      u_a0[tid] = a0;
-      u_c0[tid] = c0;
-      u_olo[tid] = olo;
-      u_nin[tid] = nin;
-      u_nout[tid] = nout;
+  if (warp == kConsumerWarps) {
+    // ---------------- producer warp: write-back of chunk it-2, then copies of chunk it
+    int issued[2] = {-1, -1};
+    bool failed = false;
+    // writes back the outputs staged in slot s by work item `prev`; false on a timeout
+    auto write_back = [&](int s, int prev) -> bool {
+      const int use = prev >> 1;
+      const bool ok = mbar_wait(&staged[s], use & 1, a.wait_limit);
+      if (!__all_sync(0xffffffffu, ok)) return false;
+      const unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
+      const int32_t *hdr = reinterpret_cast<const int32_t *>(meta_s);
+      int n_tasks = 0, n_groups = 0;
+      for (int k = 0; k < D; ++k) {
+        n_tasks += hdr[2 * k] + hdr[2 * k + 1];
+        n_groups += hdr[6 + 2 * k] + hdr[6 + 2 * k + 1];
+      }
+      const int n_oruns = hdr[13];
+      const Run *oruns = reinterpret_cast<const Run *>(meta_s + 64 + (size_t)n_tasks * sizeof(Task) +
+                                                       (size_t)n_groups * sizeof(Group));
+      const C *stage_t = D == 3 ? scr0 + (size_t)(s % S::NSCR) * a.cap1 * TS : slot0 + (size_t)s * a.cap0 * TS;
+      const unsigned char *stage = reinterpret_cast<const unsigned char *>(stage_t);
+      unsigned char *rout = gout + (size_t)(prev % a.nrhs) * a.out_rhs * sizeof(C);
+      for (int j = lane; j < n_oruns; j += 32) {
+        const Run rn = oruns[j];
+        bulk_s2g(rout + (size_t)rn.start * S::tile_bytes, stage + (size_t)rn.slot * S::tile_bytes,
+                 (unsigned)(rn.count * S::tile_bytes));
+      }
+      bulk_commit();
+      bulk_wait_read();  // the slot may be refilled after this
+      __syncwarp();
+      return true;
+    };
+    for (int it = 0; it < n_work && !failed; ++it) {
+      const int s = it & 1;
+      if (it >= 2 && !write_back(s, it - 2)) {
+        failed = true;
+        break;
+      }
+      const int ch = blockIdx.x + (it / a.nrhs) * gridDim.x, r = it % a.nrhs;
+      const ChunkDesc cd = a.chunks[ch];
+      if (a.inject_stall && it == 0) continue;  // test hook: the first chunk never arrives
+      unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
+      unsigned char *in_s = reinterpret_cast<unsigned char *>(slot0 + (size_t)s * a.cap0 * TS);
+      if (lane == 0) {
+        mbar_arrive_expect_tx(&full[s], (unsigned)(cd.blob_bytes + cd.n_in * (int)S::tile_bytes));
+        bulk_g2s(meta_s, a.blob + cd.blob_off, (unsigned)cd.blob_bytes, &full[s]);
+      }
+      __syncwarp();
+      const unsigned char *rin = gin + (size_t)r * a.in_rhs * sizeof(C);
+      for (int j = lane; j < cd.n_runs; j += 32) {
+        const Run rn = a.runs[cd.run_off + j];
+        bulk_g2s(in_s + (size_t)rn.slot * S::tile_bytes, rin + (size_t)rn.start * S::tile_bytes,
+                 (unsigned)(rn.count * S::tile_bytes), &full[s]);
+      }
+      issued[s] = it;
     }
-    int tot_in, tot_out, tot_job;
-    const int inb = block_exclusive_scan<NT>(nin, s_tmp, &tot_in);
-    const int outb = block_exclusive_scan<NT>(nout, s_tmp, &tot_out);
-    const int jobb = block_exclusive_scan<NT>(njob, s_tmp, &tot_job);
-    // ---- 2. input / output records and the job -> output map
-    if (tid < c.nu) {
-      const int iAp = u_iAp[tid], iB = u_iB[tid], a0 = u_a0[tid], c0 = u_c0[tid], olo = u_olo[tid];
-      for (int i = 0; i < nin; ++i) {
-        if (ADJ) {
-          s_in_g[inb + i] = (int64_t)(a0 + i) * a.in_row + iB;
-          s_in_code[inb + i] = a.xcode[a0 + i];
-        } else {
-          s_in_g[inb + i] = (int64_t)iAp * a.in_row + (c0 + i);
-          s_in_code[inb + i] = a.kcode[c0 + i];
-        }
-      }
-      for (int o = 0; o < nout; ++o) {
-        const int oo = olo + o;
-        if (ADJ) {
-          s_out_g[outb + o] = (int64_t)iAp * a.out_row + (c0 + oo);
-          s_out_code[outb + o] = a.kcode[c0 + oo];
-        } else {
-          s_out_g[outb + o] = (int64_t)(a0 + oo) * a.out_row + iB;
-          s_out_code[outb + o] = a.xcode[a0 + oo];
-        }
-        s_out_jb[outb + o] = jobb + o * nin;
-        s_out_inb[outb + o] = inb;
-        s_out_nin[outb + o] = nin;
-        for (int i = 0; i < nin; ++i) s_job_out[jobb + o * nin + i] = (uint16_t)(outb + o);
-      }
+    // the last two chunks' outputs
+    for (int it = (n_work >= 2 ? n_work - 2 : 0); it < n_work && !failed; ++it)
+      if (issued[it & 1] == it && !write_back(it & 1, it)) failed = true;
+    if (failed && lane == 0) atomicOr(a.status, 1);
+    // copies still in flight land before the block exits
+    for (int s = 0; s < 2; ++s) {
+      const bool ok = issued[s] < 0 || mbar_wait(&full[s], (issued[s] >> 1) & 1, a.wait_limit);
+      if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(a.status, 2);
     }
-    __syncthreads();
-    C *s_scr = s_tiles + (size_t)tot_in * PD;
+    bulk_wait_all();  // outputs written before the block exits
+    return;
+  }
 
-    for (int r = 0; r < a.nrhs; ++r) {
-      const C *rin = gin + (size_t)r * a.in_rhs;
-      C *rout = gout + (size_t)r * a.out_rhs;
-      // ---- 3. stage the input tiles
-      for (int e = tid; e < tot_in * PD; e += NT) {
-        const int t = e / PD, l = e - t * PD;
-        s_tiles[e] = rin[s_in_g[t] * PD + l];
-      }
-      __syncthreads();
-      // ---- 4. axes 0 .. D-2, one scratch tile per job
-#pragma unroll
-      for (int k = 0; k < D - 1; ++k) {
-        const int sk = ipow(P, D - 1 - k);  // element stride of axis k
-        for (int w = tid; w < tot_job * FIB; w += NT) {
-          const int j = w / FIB, f = w - j * FIB;
-          const int o = s_job_out[j];
-          const int i = j - s_out_jb[o];
-          const int tin = s_out_inb[o] + i;
-          const uint32_t ic = s_in_code[tin], oc = s_out_code[o];
-          const uint32_t xc = ADJ ? ic : oc, kc = ADJ ? oc : ic;
-          const int op = (int)((xc >> (8 * k)) & 0xffu) * 2 + (int)((kc >> k) & 1u);
-          const C *src = (k == 0) ? (s_tiles + (size_t)tin * PD) : (s_scr + (size_t)j * PD);
-          C *dst = s_scr + (size_t)j * PD;
-          const int base = (f / sk) * sk * P + (f % sk);
-          C x[P];
-#pragma unroll
-          for (int l = 0; l < P; ++l) x[l] = src[base + l * sk];
-          const C *T = s_table + (size_t)op * P * P;
-#pragma unroll
-          for (int m = 0; m < P; ++m) {
-            C y = cmk((R)0, (R)0);
-#pragma unroll
-            for (int l = 0; l < P; ++l) y = cfma(T[m * P + l], x[l], y);
-            dst[base + m * sk] = y;
-          }
-        }
-        __syncthreads();
-      }
-      // ---- 5. last axis, sum over the jobs of each output, store
-      for (int w = tid; w < tot_out * FIB; w += NT) {
-        const int o = w / FIB, f = w - o * FIB;
-        const uint32_t oc = s_out_code[o];
-        const int jb = s_out_jb[o], ib = s_out_inb[o], ni = s_out_nin[o];
-        C acc[P];
-#pragma unroll
-        for (int m = 0; m < P; ++m) acc[m] = cmk((R)0, (R)0);
-        for (int i = 0; i < ni; ++i) {
-          const uint32_t ic = s_in_code[ib + i];
-          const uint32_t xc = ADJ ? ic : oc, kc = ADJ ? oc : ic;
-          const int op = (int)((xc >> (8 * (D - 1))) & 0xffu) * 2 + (int)((kc >> (D - 1)) & 1u);
-          const C *src = s_scr + (size_t)(jb + i) * PD + f * P;
-          C x[P];
-#pragma unroll
-          for (int l = 0; l < P; ++l) x[l] = src[l];
-          const C *T = s_table + (size_t)op * P * P;
-#pragma unroll
-          for (int m = 0; m < P; ++m) {
-#pragma unroll
-            for (int l = 0; l < P; ++l) acc[m] = cfma(T[m * P + l], x[l], acc[m]);
-          }
-        }
-        C *dst = rout + s_out_g[o] * PD + f * P;
-#pragma unroll
-        for (int m = 0; m < P; ++m) dst[m] = acc[m];
-      }
-      __syncthreads();
+  // ---------------- consumer warps
+  for (int it = 0; it < n_work; ++it) {
+    const int s = it & 1, use = it >> 1;
+    const bool ok = mbar_wait(&full[s], use & 1, a.wait_limit);
+    if (consumer_any(!ok)) {  // every consumer warp leaves together
+      if (tid == 0) atomicOr(a.status, 4);
+      break;
     }
+    const unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
+    C *in_s = slot0 + (size_t)s * a.cap0 * TS;
+    C *scr = scr0 + (size_t)(s % S::NSCR) * a.cap1 * TS;
+    const int32_t *hdr = reinterpret_cast<const int32_t *>(meta_s);
+    int n_tasks = 0;
+    for (int k = 0; k < D; ++k) n_tasks += hdr[2 * k] + hdr[2 * k + 1];
+    const Task *t0 = reinterpret_cast<const Task *>(meta_s + 64);
+    const Group *g0 = reinterpret_cast<const Group *>(t0 + n_tasks);
+    const Task *t1 = t0 + hdr[0] + hdr[1];
+    const Group *g1 = g0 + hdr[6] + hdr[7];
+    run_pass<R, D, P, 0>(t0, hdr, g0, in_s, scr, s_table, warp, lane);
+    if (D == 3) {
+      const Task *t2 = t1 + hdr[2] + hdr[3];
+      const Group *g2 = g1 + hdr[8] + hdr[9];
+      run_pass<R, D, P, (D == 3 ? 1 : 0)>(t1, hdr, g1, scr, in_s, s_table, warp, lane);
+      run_pass<R, D, P, D - 1>(t2, hdr, g2, in_s, scr, s_table, warp, lane);  // staged in scr
+    } else {
+      run_pass<R, D, P, D - 1>(t1, hdr, g1, scr, in_s, s_table, warp, lane);  // staged in in_s
+    }
+    fence_async_shared();  // the staged tiles are visible to the bulk stores
+    consumer_sync();
+    if (tid == 0) mbar_arrive(&staged[s]);
   }
 }
 

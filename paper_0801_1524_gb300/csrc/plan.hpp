@@ -7,19 +7,66 @@
 
 namespace bfly {
 
-// Capacity of one block of work of the recursive step (one chunk).
-constexpr int kMaxUnits = 256;   // (A', B) units per chunk
-constexpr int kMaxIn = 256;      // input charge tiles per chunk
-constexpr int kMaxOut = 256;     // output charge tiles per chunk
-
-// A chunk: `nu` consecutive units starting at unit u0 = iAp * nB + iB.  When nu == 1 the
-// chunk may cover only outputs [o_lo, o_hi) of that unit (a unit too big for one block).
-struct Chunk {
-  int64_t u0;
-  int32_t nu;
-  int16_t o_lo, o_hi;
+// One block of work of the recursive step: a run of consecutive units (A', B), compiled
+// on the host into per-pass task lists (see make_stage_program).  Its metadata blob (a
+// 64-byte header {n_task[6], n_group[6], n_in, n_out_runs} indexed by 2*pass + phase, the
+// tasks of every pass and phase, their operator groups, then the output runs, padded to
+// 16 bytes) is copied to shared memory in one piece; its inputs are copied run by run,
+// its outputs written back run by run.
+struct ChunkDesc {
+  int32_t blob_off;   // byte offset of the blob in StageProgram::blob (16-byte aligned)
+  int32_t blob_bytes; // multiple of 16
+  int32_t run_off;    // first run in StageProgram::runs
+  int32_t n_runs;
+  int32_t n_in;       // input tiles (the runs' total)
+  int32_t n_item[3];  // items of pass 0 .. D-1 (the last pass writes the outputs)
 };
-static_assert(sizeof(Chunk) == 16, "Chunk is uploaded as 16 bytes");
+static_assert(sizeof(ChunkDesc) == 32, "ChunkDesc is uploaded as 32 bytes");
+
+// Every output tile of a pass is the sum over at most two source tiles of the previous
+// pass (pass 0: input tiles) of T^{op} applied along the pass's axis.  One task applies
+// one operator to one source: phase 0 holds the first source of every output tile (the
+// task stores), phase 1 the second sources (the task adds); each phase is sorted by
+// operator so that a thread streams many fibres through one operator.
+struct Task {
+  uint16_t src;  // chunk-local source slot
+  uint16_t dst;  // destination slot (last pass: staging slot of the output run)
+  uint16_t op;   // operator index alpha*2 + delta
+  uint16_t pad;
+};
+static_assert(sizeof(Task) == 8, "Task is uploaded as 8 bytes");
+
+// A run of tasks of one phase that share an operator; its fibres (n_tasks * P^(D-1)) are
+// processed 32 at a time ("steps"), one per warp instruction stream.
+struct Group {
+  uint16_t task_begin, n_tasks;
+  uint16_t op, step_begin;  // first step of the group within its phase
+};
+static_assert(sizeof(Group) == 8, "Group is uploaded as 8 bytes");
+
+// A run of consecutive tiles: global tiles [start, start + count) <-> chunk-local slots
+// [slot, slot + count) (inputs: copied in; outputs: written back from the staging slots).
+struct Run {
+  int32_t start;
+  uint16_t slot, count;
+};
+static_assert(sizeof(Run) == 8, "Run is uploaded as 8 bytes");
+
+struct StageProgram {
+  std::vector<ChunkDesc> chunks;
+  std::vector<unsigned char> blob;  // per chunk: header, Task[], Group[], Run[n_out_runs]
+  std::vector<Run> runs;
+  // host-side copies used for validation and statistics
+  std::vector<int32_t> in_tiles;    // global tile of every input slot, chunk after chunk
+  std::vector<int32_t> in_off;      // per chunk: first entry of in_tiles
+};
+
+// Shared-memory capacities of one block, in tiles: an input buffer holds the inputs (and
+// the pass-1 results in 3D), the scratch buffer the pass-0 results; at most max_out
+// outputs; a metadata blob of at most meta_bytes.
+struct ChunkCaps {
+  int cap0, cap1, max_out, meta_bytes;
+};
 
 // A quadtree (octree) over [0,N]^dim with unit leaves, non-empty boxes only, boxes of
 // every level in Morton order so that the children of a box are consecutive.
@@ -48,10 +95,22 @@ std::vector<double> transfer_table(int p, bool adjoint);
 // Lagrange weights of the leaf step, w_m(tau) = (G^{-1} v(tau))_m, m = 0..p-1.
 void leaf_weights(int p, double tau, double *w /* 2p doubles */);
 
-// Chunks of the recursive step at one stage.  The unit (A', B) has nout outputs and nin
-// inputs: forward nin = children of B, nout = children of A'; adjoint the reverse.  Every
-// chunk needs (inputs + outputs*inputs) tiles of shared memory.
-std::vector<Chunk> make_chunks(const std::vector<int32_t> &csAp, const std::vector<int32_t> &csB,
-                               bool adjoint, int tile_cap);
+// The recursive step at stage t as chunk programs.  Forward: unit (A', B) reads the tiles
+// f^{A'Bc} of the children Bc of B and writes f^{AB} for the children A of A'; adjoint:
+// reads f^{AB} of the children A, writes f^{A'Bc}.  The operator of every (A, Bc) pair is
+// (x)_d T^{(alpha_d(A), delta_d(Bc))}; passes apply one axis each and sum, before each
+// axis, the sources that agree on all bits still to be applied (sum factorisation).
+//   csAp : children of the A' boxes (T_X level L-t-1 -> L-t), xidx: box indices of level L-t
+//   csB  : children of the B boxes (T_K level t -> t+1),       kidx: box indices of level t+1
+//   in_row / out_row: tiles per row of the input / output stage buffer.
+StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp,
+                                const std::vector<int32_t> &xidx, const std::vector<int32_t> &csB,
+                                const std::vector<int32_t> &kidx, bool adjoint, ChunkCaps caps);
+
+// Checks every index of a compiled stage program against the capacities it was compiled
+// for and the number of tiles of its input and output stage buffers; returns "" or a
+// description of the first violation.
+std::string validate_program(const StageProgram &prog, int dim, ChunkCaps caps, int64_t in_tiles,
+                             int64_t out_tiles);
 
 }  // namespace bfly

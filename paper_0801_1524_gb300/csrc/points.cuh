@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) spread_kernel(const PointArgs a) {
     for (int d = 1; d < D; ++d) wt = cmul(wt, W[((size_t)j * D + d) * P + ld[d]]);
     acc = a.conj ? cfma_conj(wt, v, acc) : cfma(wt, v, acc);
   }
-  reinterpret_cast<C *>(a.vout)[(size_t)r * a.tile_rhs + (size_t)b * PD + l] = acc;
+  reinterpret_cast<C *>(a.vout)[(size_t)r * a.tile_rhs + (size_t)b * a.tile_stride + l] = acc;
 }
 
 // val_i = sum_l prod_d W_i[d][l_d] tile[leaf(i)][l]   (conj(W) when a.conj)
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) interp_kernel(const PointArgs a) {
 #pragma unroll
     for (int l = 0; l < P; ++l) w[d][l] = a.conj ? cconj(W[d * P + l]) : W[d * P + l];
   const C *tile = reinterpret_cast<const C *>(a.vin) + (size_t)r * a.tile_rhs +
-                  (size_t)a.point_leaf[i] * PD;
+                  (size_t)a.point_leaf[i] * a.tile_stride;
   C acc = cmk((R)0, (R)0);
   if (D == 2) {
 #pragma unroll

@@ -12,6 +12,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "UNSUPPOR
 BFLY_C64, BFLY_C128 = 0, 1
 BFLY_PREC_FP64, BFLY_PREC_FP32 = 0, 1
 BFLY_FLAG_HOST_ONLY = 1
+BFLY_FLAG_TEST_STALL = 2
 
 # Every function the header declares, with (restype, argtypes).
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -29,7 +30,7 @@ class PlanInfo(ctypes.Structure):
                 ("max_pairs", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("tiles_read_fwd", ctypes.c_int64), ("tiles_written_fwd", ctypes.c_int64),
                 ("jobs_fwd", ctypes.c_int64), ("chunks_fwd", ctypes.c_int64),
-                ("plan_seconds", ctypes.c_double)]
+                ("flops_fwd", ctypes.c_double), ("plan_seconds", ctypes.c_double)]
 
 
 SIGNATURES = {
@@ -42,6 +43,7 @@ SIGNATURES = {
     "bfly_direct": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "bfly_execute_events": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp, ctypes.POINTER(_vp), _i]),
     "bfly_plan_info": (_i, [_vp, ctypes.POINTER(PlanInfo)]),
+    "bfly_device_status": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "bfly_plan_stage": (_i, [_vp, _i, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "bfly_last_error": (ctypes.c_char_p, []),
     "bfly_version": (ctypes.c_char_p, []),

@@ -41,7 +41,7 @@ class Plan:
     """
 
     def __init__(self, x, k, N: float, p: int, precision: str = "fp32", max_nrhs: int = 1,
-                 host_only: bool = False, smem_kb: int = 0):
+                 host_only: bool = False, smem_kb: int = 0, flags: int = 0):
         lib = native.load()
         x = np.ascontiguousarray(x, dtype=np.float64)
         k = np.ascontiguousarray(k, dtype=np.float64)
@@ -58,7 +58,7 @@ class Plan:
         opts = native.Opts()
         opts.prec = PRECISIONS[precision]
         opts.max_nrhs = self.max_nrhs
-        opts.flags = native.BFLY_FLAG_HOST_ONLY if host_only else 0
+        opts.flags = (native.BFLY_FLAG_HOST_ONLY if host_only else 0) | int(flags)
         opts.smem_kb = int(smem_kb)
         h = ctypes.c_void_p()
         self._lib = lib
@@ -87,6 +87,14 @@ class Plan:
         self.close()
 
     # ---- introspection
+    def device_status(self) -> int:
+        """Waits for the device, reads and clears the status word (0 = no wait gave up)."""
+        flags = ctypes.c_int(0)
+        st = self._lib.bfly_device_status(self._h, ctypes.byref(flags))
+        if st not in (native.BFLY_OK, 5):
+            native.check(st, "bfly_device_status")
+        return flags.value
+
     def info(self) -> dict:
         inf = native.PlanInfo()
         native.check(self._lib.bfly_plan_info(self._h, ctypes.byref(inf)), "bfly_plan_info")
