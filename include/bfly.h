@@ -156,6 +156,27 @@ bfly_status bfly_execute_events(bfly_plan_t plan, const void *in, void *out, int
                                 int n_events);
 
 /*
+ * bfly_execute_noalloc — bfly_execute (forward, device buffers) without any allocation:
+ * the two charge buffers of the sweep come from a static device array owned by the
+ * library (64 MiB in all, 32 MiB per buffer) instead of the plan's workspace.  The paper
+ * has no counterpart; this entry point serves callers that cannot allocate device memory
+ * when they run the transform (inside a CUDA graph capture, where cudaMalloc is not
+ * allowed; under an external allocator or memory budget; or many plans sharing one fixed
+ * workspace).  The plan itself must have been created beforehand.
+ *   - Sizes: max_pairs * tile * element bytes * nrhs must fit in 32 MiB, otherwise the call
+ *     returns BFLY_ERR_INVALID_ARG and says so; nothing is launched then.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current and caches it: make that first call before any stream
+ *     capture.  The call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ *     routine).
+ *   - Every call shares the array and it keeps the last call's contents (nothing in it
+ *     needs clearing): calls that overlap on the GPU (other streams, other threads) race.
+ * Arguments, layouts and results are those of bfly_execute.
+ */
+bfly_status bfly_execute_noalloc(bfly_plan_t plan, const void *f, void *u, int nrhs, int dtype,
+                                 void *stream);
+
+/*
  * bfly_device_status — waits for the device, then reads and clears the plan's device
  * status word.  Kernels whose bounded waits gave up set bits in it (1: the copy engine
  * side gave up waiting for a free buffer, 2: copies were still in flight at exit, 4: the

@@ -46,37 +46,10 @@ const KernelSet *select_kernels(int p, int prec, int dim) {
 
 }  // namespace
 
-struct bfly_plan_s {
-  int dim = 0, p = 0, L = 0, prec = 1, max_nrhs = 1;
-  unsigned flags = 0;
-  double N = 0;
-  int64_t nx = 0, nk = 0;
-  int device = -1;
-  HostTree TX, TK;
-  const KernelSet *ks = nullptr;
-  ChunkCaps caps{};
-  int level_grid = 0, TS = 0;
-  size_t level_smem = 0, elem_bytes = 0;
-  std::vector<StageProgram> progF, progA;  // per stage t in [0, L-1]
-  std::vector<int64_t> pairs;              // per stage t in [0, L]
-  // device memory: one allocation carved into the arrays below
-  char *dmem = nullptr;
-  size_t dbytes = 0;
-  int32_t *perm_x = nullptr, *perm_k = nullptr, *leaf_x = nullptr, *leaf_k = nullptr;
-  int32_t *pleaf_x = nullptr, *pleaf_k = nullptr, *lidx_x = nullptr;
-  double *off_x = nullptr, *off_k = nullptr, *xs = nullptr, *ks_ = nullptr, *inv_den = nullptr;
-  void *Wx = nullptr, *Wk = nullptr, *table = nullptr, *tableH = nullptr;
-  struct DevProg {
-    bfly::ChunkDesc *chunks = nullptr;
-    unsigned char *blob = nullptr;
-    bfly::Run *runs = nullptr;
-  };
-  int *status = nullptr;  // device status word (bfly_device_status)
-  std::vector<DevProg> dF, dA;  // per stage t in [0, L-1]
-  void *buf[2] = {nullptr, nullptr};
-  void *stage_in = nullptr, *stage_out = nullptr;
-  bfly_plan_info_t info{};
-};
+#include "plan_state.hpp"
+
+using bfly_state::level_args;
+using bfly_state::point_args;
 
 namespace {
 
@@ -109,6 +82,10 @@ bool is_pow2(double N, int *L) {
 }
 
 }  // namespace
+
+namespace bfly_state {
+bfly_status set_error(bfly_status s, const std::string &msg) { return fail(s, msg); }
+}  // namespace bfly_state
 
 extern "C" {
 
@@ -395,52 +372,6 @@ bfly_status check_exec(bfly_plan_t P, const void *a, const void *b, int nrhs, in
   if (dtype != BFLY_C64 && dtype != BFLY_C128) return fail(BFLY_ERR_INVALID_ARG, "unknown dtype");
   return BFLY_OK;
 }
-
-bfly::PointArgs point_args(bfly_plan_t P, bool x_side, const void *vin, void *vout, int nrhs,
-                           bool io64, bool conj, int64_t tile_rhs) {
-  bfly::PointArgs a{};
-  a.vin = vin;
-  a.vout = vout;
-  a.nrhs = nrhs;
-  a.io64 = io64;
-  a.conj = conj;
-  a.tile_rhs = tile_rhs;
-  a.tile_stride = P->TS;
-  const HostTree &T = x_side ? P->TX : P->TK;
-  a.n_total = T.n;
-  a.nbox = T.nbox(P->L);
-  a.perm = x_side ? P->perm_x : P->perm_k;
-  a.leaf_start = x_side ? P->leaf_x : P->leaf_k;
-  a.point_leaf = x_side ? P->pleaf_x : P->pleaf_k;
-  a.W = x_side ? P->Wx : P->Wk;
-  return a;
-}
-
-bfly::LevelArgs level_args(bfly_plan_t P, int t, bool adjoint, int nrhs) {
-  bfly::LevelArgs a{};
-  void *bt = P->buf[t & 1], *bt1 = P->buf[(t + 1) & 1];
-  const StageProgram &pg = adjoint ? P->progA[t] : P->progF[t];
-  const bfly_plan_s::DevProg &dp = adjoint ? P->dA[t] : P->dF[t];
-  a.in = adjoint ? bt : bt1;
-  a.out = adjoint ? bt1 : bt;
-  a.in_rhs = (adjoint ? P->pairs[t] : P->pairs[t + 1]) * P->TS;
-  a.out_rhs = (adjoint ? P->pairs[t + 1] : P->pairs[t]) * P->TS;
-  a.nrhs = nrhs;
-  a.chunks = dp.chunks;
-  a.nchunks = (int)pg.chunks.size();
-  a.blob = dp.blob;
-  a.runs = dp.runs;
-  a.table = adjoint ? P->tableH : P->table;
-  a.cap0 = P->caps.cap0;
-  a.cap1 = P->caps.cap1;
-  a.meta_bytes = P->caps.meta_bytes;
-  const bool stall = (P->flags & BFLY_FLAG_TEST_STALL) != 0;
-  a.wait_limit = stall ? 2000000LL : 2000000000LL;  // ~1 ms / ~1 s of SM clock
-  a.status = P->status;
-  a.inject_stall = stall ? 1 : 0;
-  return a;
-}
-
 
 // Launches the sweep on stream s; when ev is non-null, records ev[i] before launch i and
 // ev[L+2] after the last one.

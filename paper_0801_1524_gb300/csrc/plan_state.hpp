@@ -1,0 +1,95 @@
+// Internal state of a plan and the argument blocks of its kernels, shared by the
+// translation units of the C ABI (api.cu, noalloc.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "../../include/bfly.h"
+#include "kernels.hpp"
+#include "plan.hpp"
+
+struct bfly_plan_s {
+  int dim = 0, p = 0, L = 0, prec = 1, max_nrhs = 1;
+  unsigned flags = 0;
+  double N = 0;
+  int64_t nx = 0, nk = 0;
+  int device = -1;
+  bfly::HostTree TX, TK;
+  const bfly::KernelSet *ks = nullptr;
+  bfly::ChunkCaps caps{};
+  int level_grid = 0, TS = 0;
+  size_t level_smem = 0, elem_bytes = 0;
+  std::vector<bfly::StageProgram> progF, progA;  // per stage t in [0, L-1]
+  std::vector<int64_t> pairs;              // per stage t in [0, L]
+  // device memory: one allocation carved into the arrays below
+  char *dmem = nullptr;
+  size_t dbytes = 0;
+  int32_t *perm_x = nullptr, *perm_k = nullptr, *leaf_x = nullptr, *leaf_k = nullptr;
+  int32_t *pleaf_x = nullptr, *pleaf_k = nullptr, *lidx_x = nullptr;
+  double *off_x = nullptr, *off_k = nullptr, *xs = nullptr, *ks_ = nullptr, *inv_den = nullptr;
+  void *Wx = nullptr, *Wk = nullptr, *table = nullptr, *tableH = nullptr;
+  struct DevProg {
+    bfly::ChunkDesc *chunks = nullptr;
+    unsigned char *blob = nullptr;
+    bfly::Run *runs = nullptr;
+  };
+  int *status = nullptr;  // device status word (bfly_device_status)
+  std::vector<DevProg> dF, dA;  // per stage t in [0, L-1]
+  void *buf[2] = {nullptr, nullptr};
+  void *stage_in = nullptr, *stage_out = nullptr;
+  bfly_plan_info_t info{};
+};
+
+namespace bfly_state {
+
+// Records `msg` as the calling thread's last error and returns `s`.
+bfly_status set_error(bfly_status s, const std::string &msg);
+
+inline bfly::PointArgs point_args(bfly_plan_t P, bool x_side, const void *vin, void *vout, int nrhs,
+                           bool io64, bool conj, int64_t tile_rhs) {
+  bfly::PointArgs a{};
+  a.vin = vin;
+  a.vout = vout;
+  a.nrhs = nrhs;
+  a.io64 = io64;
+  a.conj = conj;
+  a.tile_rhs = tile_rhs;
+  a.tile_stride = P->TS;
+  const bfly::HostTree &T = x_side ? P->TX : P->TK;
+  a.n_total = T.n;
+  a.nbox = T.nbox(P->L);
+  a.perm = x_side ? P->perm_x : P->perm_k;
+  a.leaf_start = x_side ? P->leaf_x : P->leaf_k;
+  a.point_leaf = x_side ? P->pleaf_x : P->pleaf_k;
+  a.W = x_side ? P->Wx : P->Wk;
+  return a;
+}
+
+inline bfly::LevelArgs level_args(bfly_plan_t P, int t, bool adjoint, int nrhs) {
+  bfly::LevelArgs a{};
+  void *bt = P->buf[t & 1], *bt1 = P->buf[(t + 1) & 1];
+  const bfly::StageProgram &pg = adjoint ? P->progA[t] : P->progF[t];
+  const bfly_plan_s::DevProg &dp = adjoint ? P->dA[t] : P->dF[t];
+  a.in = adjoint ? bt : bt1;
+  a.out = adjoint ? bt1 : bt;
+  a.in_rhs = (adjoint ? P->pairs[t] : P->pairs[t + 1]) * P->TS;
+  a.out_rhs = (adjoint ? P->pairs[t + 1] : P->pairs[t]) * P->TS;
+  a.nrhs = nrhs;
+  a.chunks = dp.chunks;
+  a.nchunks = (int)pg.chunks.size();
+  a.blob = dp.blob;
+  a.runs = dp.runs;
+  a.table = adjoint ? P->tableH : P->table;
+  a.cap0 = P->caps.cap0;
+  a.cap1 = P->caps.cap1;
+  a.meta_bytes = P->caps.meta_bytes;
+  const bool stall = (P->flags & BFLY_FLAG_TEST_STALL) != 0;
+  a.wait_limit = stall ? 2000000LL : 2000000000LL;  // ~1 ms / ~1 s of SM clock
+  a.status = P->status;
+  a.inject_stall = stall ? 1 : 0;
+  return a;
+}
+
+
+}  // namespace bfly_state

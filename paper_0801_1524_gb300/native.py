@@ -8,6 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbfly.so")
 
 BFLY_OK = 0
+BFLY_ERR_INVALID_ARG = 1
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "UNSUPPORTED", 5: "TIMEOUT"}
 BFLY_C64, BFLY_C128 = 0, 1
 BFLY_PREC_FP64, BFLY_PREC_FP32 = 0, 1
@@ -38,6 +39,7 @@ SIGNATURES = {
                               ctypes.POINTER(Opts)]),
     "bfly_plan_destroy": (None, [_vp]),
     "bfly_execute": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
+    "bfly_execute_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "bfly_execute_adjoint": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "bfly_execute_host": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "bfly_direct": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),

@@ -137,6 +137,12 @@ class Plan:
     def forward(self, f, out=None, stream=None):
         return self._run(self._lib.bfly_execute, f, self.nk, self.nx, out, stream, "bfly_execute")
 
+    def forward_noalloc(self, f, out=None, stream=None):
+        """bfly_execute_noalloc: the forward transform with the library's static workspace
+        (for callers that cannot allocate device memory at that point; see bfly.h)."""
+        return self._run(self._lib.bfly_execute_noalloc, f, self.nk, self.nx, out, stream,
+                         "bfly_execute_noalloc")
+
     def adjoint(self, u, out=None, stream=None):
         return self._run(self._lib.bfly_execute_adjoint, u, self.nx, self.nk, out, stream,
                          "bfly_execute_adjoint")
