@@ -28,6 +28,7 @@ extern "C" {
 #endif
 
 typedef struct bfly_plan_s *bfly_plan_t;
+typedef struct bfly_batch_s *bfly_batch_t;
 
 typedef enum {
   BFLY_OK = 0,
@@ -184,6 +185,30 @@ bfly_status bfly_execute_noalloc(bfly_plan_t plan, const void *f, void *u, int n
  * the bits.  Returns BFLY_ERR_TIMEOUT when any bit was set, else BFLY_OK.
  */
 bfly_status bfly_device_status(bfly_plan_t plan, int *flags);
+
+/*
+ * Batches: many independent transforms (each the operation of bfly_execute, Sec. 2.2)
+ * run together.  The paper has no counterpart; a batch groups plans of equal dim, p and
+ * precision (different N and point sets), aligned at the final stage, and runs one
+ * launch of the recursive step per stage over the work of every plan.
+ *
+ * bfly_batch_create — plans: count device plans (the caller keeps ownership and must
+ *   keep them alive while the batch exists).  Errors: INVALID_ARG (NULL, host-only plans,
+ *   mixed dim / p / precision / device), OUT_OF_MEMORY, CUDA.
+ * bfly_batch_execute — f[i] (device, [nrhs][nk_i]) -> u[i] (device, [nrhs][nx_i]) for
+ *   every plan i, nrhs <= every plan's max_nrhs, asynchronous on `stream`.  On a
+ *   non-default stream the launches are captured into a CUDA graph the first time and
+ *   the graph is replayed while f, u, nrhs, dtype and stream are unchanged (other values
+ *   capture a new graph); on the default stream the launches are issued directly.  The
+ *   batch uses the plans' workspaces: do not execute those plans concurrently.
+ * bfly_batch_status — like bfly_device_status for the batch's launches.
+ * bfly_batch_destroy — frees the batch (not the plans); NULL is ignored.
+ */
+bfly_status bfly_batch_create(bfly_batch_t *out, int count, const bfly_plan_t *plans);
+bfly_status bfly_batch_execute(bfly_batch_t batch, const void *const *f, void *const *u, int nrhs,
+                               int dtype, void *stream);
+bfly_status bfly_batch_status(bfly_batch_t batch, int *flags);
+void bfly_batch_destroy(bfly_batch_t batch);
 
 /* Sizes and counts of the plan (host data; no device access). */
 bfly_status bfly_plan_info(bfly_plan_t plan, bfly_plan_info_t *info);

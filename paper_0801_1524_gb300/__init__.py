@@ -4,7 +4,7 @@ this package only marshals arguments.  Importing it does not load the library; t
 Plan does, and raises if the library is missing or unusable."""
 import importlib
 
-__all__ = ["Plan", "butterfly", "butterfly_fn"]
+__all__ = ["Plan", "Batch", "butterfly", "butterfly_fn"]
 
 
 def __getattr__(name):

@@ -93,6 +93,7 @@ struct LevelArgs {
   long long wait_limit;         // clock cycles before a wait gives up
   int *status;                  // device status word: bits set on a timeout
   int inject_stall;             // test hook: withhold the copies of the first chunk
+  const BatchEntry *entries;    // batched launch: per-chunk chunk and buffers (else null)
 };
 
 // Steps 2 and 4 and their adjoints: per-point weights against one tile per leaf.

@@ -8,7 +8,8 @@
 // agree on every bit still to be applied; sum factorisation):
 //   inputs --pass 0--> scratch --pass 1 (3D)--> input slot --last pass--> global.
 // The adjoint sweep runs the same kernel on the adjoint program with the
-// conjugate-transposed operators.
+// conjugate-transposed operators.  A batched launch runs the chunks of many plans (same
+// dim, p and precision): a per-chunk entry then names the chunk's buffers.
 //
 // A persistent block is warp-specialised.  One producer warp walks over the block's
 // chunks (times right-hand sides).  For chunk i in slot s = i mod 2 it first writes back
@@ -278,7 +279,14 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
                                                        (size_t)n_groups * sizeof(Group));
       const C *stage_t = D == 3 ? scr0 + (size_t)(s % S::NSCR) * a.cap1 * TS : slot0 + (size_t)s * a.cap0 * TS;
       const unsigned char *stage = reinterpret_cast<const unsigned char *>(stage_t);
-      unsigned char *rout = gout + (size_t)(prev % a.nrhs) * a.out_rhs * sizeof(C);
+      unsigned char *obase = gout;
+      int64_t orhs = a.out_rhs;
+      if (a.entries) {
+        const BatchEntry &be = a.entries[blockIdx.x + (prev / a.nrhs) * gridDim.x];
+        obase = reinterpret_cast<unsigned char *>(be.out);
+        orhs = be.out_rhs;
+      }
+      unsigned char *rout = obase + (size_t)(prev % a.nrhs) * orhs * sizeof(C);
       for (int j = lane; j < n_oruns; j += 32) {
         const Run rn = oruns[j];
         bulk_s2g(rout + (size_t)rn.start * S::tile_bytes, stage + (size_t)rn.slot * S::tile_bytes,
@@ -296,18 +304,23 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
         break;
       }
       const int ch = blockIdx.x + (it / a.nrhs) * gridDim.x, r = it % a.nrhs;
-      const ChunkDesc cd = a.chunks[ch];
+      const ChunkDesc cd = a.entries ? a.entries[ch].d : a.chunks[ch];
+      const unsigned char *blob = a.entries ? a.entries[ch].blob : a.blob;
+      const Run *runs = a.entries ? a.entries[ch].runs : a.runs;
+      const unsigned char *ibase =
+          a.entries ? reinterpret_cast<const unsigned char *>(a.entries[ch].in) : gin;
+      const int64_t irhs = a.entries ? a.entries[ch].in_rhs : a.in_rhs;
       if (a.inject_stall && it == 0) continue;  // test hook: the first chunk never arrives
       unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
       unsigned char *in_s = reinterpret_cast<unsigned char *>(slot0 + (size_t)s * a.cap0 * TS);
       if (lane == 0) {
         mbar_arrive_expect_tx(&full[s], (unsigned)(cd.blob_bytes + cd.n_in * (int)S::tile_bytes));
-        bulk_g2s(meta_s, a.blob + cd.blob_off, (unsigned)cd.blob_bytes, &full[s]);
+        bulk_g2s(meta_s, blob + cd.blob_off, (unsigned)cd.blob_bytes, &full[s]);
       }
       __syncwarp();
-      const unsigned char *rin = gin + (size_t)r * a.in_rhs * sizeof(C);
+      const unsigned char *rin = ibase + (size_t)r * irhs * sizeof(C);
       for (int j = lane; j < cd.n_runs; j += 32) {
-        const Run rn = a.runs[cd.run_off + j];
+        const Run rn = runs[cd.run_off + j];
         bulk_g2s(in_s + (size_t)rn.slot * S::tile_bytes, rin + (size_t)rn.start * S::tile_bytes,
                  (unsigned)(rn.count * S::tile_bytes), &full[s]);
       }

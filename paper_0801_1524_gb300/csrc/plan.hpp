@@ -52,6 +52,17 @@ struct Run {
 };
 static_assert(sizeof(Run) == 8, "Run is uploaded as 8 bytes");
 
+// A chunk of a batched launch: the chunk and the buffers of the plan it belongs to.
+struct BatchEntry {
+  ChunkDesc d;
+  const unsigned char *blob;
+  const Run *runs;
+  const void *in;
+  void *out;
+  int64_t in_rhs, out_rhs;  // elements between right-hand sides of the plan's buffers
+};
+static_assert(sizeof(BatchEntry) == 80, "BatchEntry is uploaded as 80 bytes");
+
 struct StageProgram {
   std::vector<ChunkDesc> chunks;
   std::vector<unsigned char> blob;  // per chunk: header, Task[], Group[], Run[n_out_runs]

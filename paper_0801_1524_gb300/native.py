@@ -45,6 +45,10 @@ SIGNATURES = {
     "bfly_direct": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "bfly_execute_events": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp, ctypes.POINTER(_vp), _i]),
     "bfly_plan_info": (_i, [_vp, ctypes.POINTER(PlanInfo)]),
+    "bfly_batch_create": (_i, [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp)]),
+    "bfly_batch_execute": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _i, _vp]),
+    "bfly_batch_status": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "bfly_batch_destroy": (None, [_vp]),
     "bfly_device_status": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "bfly_plan_stage": (_i, [_vp, _i, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "bfly_last_error": (ctypes.c_char_p, []),

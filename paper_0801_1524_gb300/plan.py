@@ -177,6 +177,53 @@ class Plan:
         return out[0] if np.ndim(v) == 1 else out
 
 
+class Batch:
+    """Many plans (same dim, p, precision) executed together: one launch of the recursive
+    step per stage over all of them, captured in a CUDA graph on a non-default stream."""
+
+    def __init__(self, plans):
+        self._lib = native.load()
+        self.plans = list(plans)  # kept alive with the batch
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h for p in self.plans])
+        h = ctypes.c_void_p()
+        self._h = None
+        native.check(self._lib.bfly_batch_create(ctypes.byref(h), len(self.plans), arr),
+                     "bfly_batch_create")
+        self._h = h
+
+    def close(self):
+        if self._h is not None:
+            self._lib.bfly_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, fs, us=None, stream=None):
+        """fs: list of [nrhs, nk_i] CUDA tensors (same dtype); returns / fills us."""
+        torch = _torch()
+        fs = [f.reshape(-1, p.nk).contiguous() for f, p in zip(fs, self.plans)]
+        nrhs = fs[0].shape[0]
+        if us is None:
+            us = [torch.empty((nrhs, p.nx), dtype=fs[0].dtype, device=fs[0].device) for p in self.plans]
+        fa = (ctypes.c_void_p * len(fs))(*[f.data_ptr() for f in fs])
+        ua = (ctypes.c_void_p * len(us))(*[u.data_ptr() for u in us])
+        native.check(self._lib.bfly_batch_execute(self._h, fa, ua, nrhs, _dtype_code(fs[0]),
+                                                  _stream_ptr(stream)), "bfly_batch_execute")
+        self._keep = (fs, us)  # the device buffers must outlive the asynchronous launches
+        return us
+
+    def device_status(self) -> int:
+        flags = ctypes.c_int(0)
+        st = self._lib.bfly_batch_status(self._h, ctypes.byref(flags))
+        if st not in (native.BFLY_OK, 5):
+            native.check(st, "bfly_batch_status")
+        return flags.value
+
+
 def butterfly_fn():
     """torch.autograd.Function u = B f with du/df handled by the adjoint sweep."""
     torch = _torch()

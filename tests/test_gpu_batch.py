@@ -1,0 +1,58 @@
+"""Batched execution: instances of uneven N (star-shaped curve pairs), several right-hand
+sides each, one recursive-step launch per stage over all of them, captured in a CUDA
+graph on a side stream and replayed.  Every instance must equal its own plan's forward
+transform (the same per-chunk arithmetic) and match the oracle."""
+import numpy as np
+import pytest
+
+import oracle.butterfly as ob
+from conftest import rel_l2
+from paper_0801_1524_gb300 import workloads as w
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _instances():
+    out = []
+    for i, N in enumerate([64.0, 512.0, 128.0, 1024.0, 32.0, 256.0]):
+        x = w.sample_curve(w.star_curve(2 * i + 1000), N)
+        k = w.sample_curve(w.star_curve(2 * i + 1001), N)
+        out.append(w.Instance(f"b{i}", 2, N, 7, x, k, nrhs=3, f_seed=i))
+    return out
+
+
+@pytest.mark.parametrize("prec,dtype", [("fp32", torch.complex64), ("fp64", torch.complex128)])
+def test_batch_matches_plans_and_oracle(prec, dtype):
+    from paper_0801_1524_gb300.plan import Batch, Plan
+    insts = _instances()
+    plans = [Plan(I.x, I.k, I.N, I.p, precision=prec, max_nrhs=3) for I in insts]
+    batch = Batch(plans)
+    fs = [torch.as_tensor(I.sources(), dtype=dtype, device="cuda") for I in insts]
+    ref = [P.forward(f) for P, f in zip(plans, fs)]
+    us = batch.forward(fs)  # default stream: direct launches
+    torch.cuda.synchronize()
+    for u, r in zip(us, ref):
+        assert torch.equal(u, r)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        us2 = [torch.empty_like(r) for r in ref]
+        for _ in range(3):  # capture, then replays
+            batch.forward(fs, us2, stream=side)
+    side.synchronize()
+    for u, r in zip(us2, ref):
+        assert torch.equal(u, r)
+    assert batch.device_status() == 0
+    tol = 1e-6 if prec == "fp32" else 1e-9
+    for I, u in zip(insts[:4], us):
+        oracle = ob.butterfly(I.x, I.k, I.sources(), I.N, I.p)
+        assert rel_l2(u.cpu().numpy().astype(np.complex128), oracle) < tol
+
+
+def test_batch_rejects_mixed_plans():
+    from paper_0801_1524_gb300.plan import Batch, Plan
+    from paper_0801_1524_gb300.native import BflyError
+    a = w.small_random(2, 64.0, 7, 100, 100, 1)
+    b = w.small_random(2, 64.0, 5, 100, 100, 2)
+    with pytest.raises(BflyError):
+        Batch([Plan(a.x, a.k, a.N, 7), Plan(b.x, b.k, b.N, 5)])
