@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target wall time of the oracle CPU baseline sample")
     ap.add_argument("--no-baselines", action="store_true")
+    ap.add_argument("--nrhs", type=int, default=16, help="right-hand sides (star_batch)")
+    ap.add_argument("--autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -383,8 +385,72 @@ def main_reference(args, rank):
             "wall_s": wall}
 
 
+def main_batch(args):
+    """64 star-curve instances (N log-uniform in [512, 16384] rounded to powers of two),
+    p = 7, nrhs complex64 right-hand sides each, one graph replay per step."""
+    import torch
+    from paper_0801_1524_gb300 import workloads as w
+    from paper_0801_1524_gb300.plan import Batch, Plan
+    insts = w.star_batch(nrhs=args.nrhs)
+    dev = torch.device("cuda", 0)
+    out = {}
+    smem_kb = 0
+    if args.autotune:  # one configuration for the whole batch, tuned on its largest instance
+        big = max(insts, key=lambda I: I.N)
+        smem_kb = Plan(big.x, big.k, big.N, big.p, max_nrhs=args.nrhs, autotune=True).info()["smem_kb"]
+    for prec, dtype in (("fp32", torch.complex64), ("fp64", torch.complex128)):
+        plans = [Plan(I.x, I.k, I.N, I.p, precision=prec, max_nrhs=args.nrhs,
+                      smem_kb=smem_kb if prec == "fp32" else 0) for I in insts]
+        batch = Batch(plans)
+        fs = [torch.as_tensor(I.sources(dtype=np.complex64), device=dev).to(dtype) for I in insts]
+        us = [torch.empty((args.nrhs, I.x.shape[0]), dtype=dtype, device=dev) for I in insts]
+        side = torch.cuda.Stream()
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        steps = args.steps if prec == "fp32" else max(3, min(args.steps, 10))
+        with torch.cuda.stream(side):
+            for _ in range(max(args.warmup, 3)):
+                batch.forward(fs, us, stream=side)
+            evs = []
+            for _ in range(steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(side)
+                batch.forward(fs, us, stream=side)
+                b.record(side)
+                evs.append((a, b))
+        side.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        out[prec] = {"ms": ms, "us": [u.to(torch.complex128) for u in us],
+                     "status": batch.device_status(),
+                     "flops": sum(p.info()["flops_fwd"] for p in plans) * args.nrhs}
+        del batch, plans
+    u32, u64 = out["fp32"]["us"], out["fp64"]["us"]
+    num = sum(torch.linalg.norm(a - b).item() ** 2 for a, b in zip(u32, u64))
+    den = sum(torch.linalg.norm(b).item() ** 2 for b in u64)
+    pairs = sum(I.x.shape[0] * I.k.shape[0] for I in insts) * args.nrhs
+    ms = out["fp32"]["ms"]
+    line = {"metric": METRIC + " (batched)", "value": len(insts) * args.nrhs * 1e3 / ms,
+            "unit": "instance-RHS transforms/s", "ms_per_step": ms, "steps": args.steps,
+            "warmup": args.warmup, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"star_batch: 64 instances, N in 512..16384 (powers of two), p=7, "
+                                   f"{args.nrhs} complex64 RHS, graph replay",
+                       "sum_N": float(sum(I.N for I in insts)),
+                       "points": int(sum(I.x.shape[0] + I.k.shape[0] for I in insts))},
+            "effective_IJ_per_s": pairs * 1e3 / ms,
+            "fp64_batch_ms": out["fp64"]["ms"], "speedup_vs_fp64": out["fp64"]["ms"] / ms,
+            "rel_l2_fp32_vs_fp64": (num / den) ** 0.5,
+            "recursive_tflops": out["fp32"]["flops"] / (ms * 1e-3) / 1e12,
+            "status": [out["fp32"]["status"], out["fp64"]["status"]], "smem_kb": smem_kb or None}
+    return line
+
+
 def main():
     args = parse()
+    if args.workload == "star_batch":
+        import __graft_entry__
+        __graft_entry__.build()
+        print(json.dumps(main_batch(args)), flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

@@ -54,12 +54,20 @@ typedef enum { BFLY_PREC_FP64 = 0, BFLY_PREC_FP32 = 1 } bfly_precision;
  * waits time out and set the device status word (results are then invalid). */
 #define BFLY_FLAG_TEST_STALL 2u
 
+/* Autotune the recursive step: build the plan for each candidate shared-memory budget
+ * per block (which sets how much work one block takes at a time and how many blocks
+ * share an SM), time a forward sweep of each with max_nrhs right-hand sides, and keep
+ * the fastest.  With tune_cache set, a choice recorded there for the same GPU, dim, p,
+ * precision, nrhs and size class is reused, and new choices are appended. */
+#define BFLY_FLAG_AUTOTUNE 4u
+
 typedef struct {
-  int prec;          /* bfly_precision; default BFLY_PREC_FP32 */
-  int max_nrhs;      /* workspace is sized for up to this many right-hand sides (>= 1) */
-  unsigned flags;    /* BFLY_FLAG_* */
-  int smem_kb;       /* shared memory per block for the recursive step, 0 = default */
-  int reserved[4];   /* must be zero */
+  int prec;                /* bfly_precision; default BFLY_PREC_FP32 */
+  int max_nrhs;            /* workspace is sized for up to this many right-hand sides (>= 1) */
+  unsigned flags;          /* BFLY_FLAG_* */
+  int smem_kb;             /* shared memory per block for the recursive step, 0 = default */
+  const char *tune_cache;  /* autotuning cache file (text), or NULL */
+  int reserved[2];         /* must be zero */
 } bfly_opts;
 
 typedef struct {
@@ -75,6 +83,9 @@ typedef struct {
   int64_t jobs_fwd;             /* (output box pair, child) pairs of the recursive step */
   int64_t chunks_fwd;           /* blocks of work of the recursive step, all stages */
   double flops_fwd;             /* real flops of the recursive step as executed, one RHS */
+  int smem_kb;                  /* shared-memory budget per block of the recursive step */
+  int blocks_per_sm;            /* resident blocks of the recursive step per SM */
+  double tuned_ms;              /* autotuning: time of the chosen candidate (0 if not tuned) */
   double plan_seconds;          /* host wall time of bfly_plan_create */
 } bfly_plan_info_t;
 

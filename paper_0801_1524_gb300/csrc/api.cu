@@ -1,6 +1,8 @@
 // C ABI of the butterfly (include/bfly.h): plan creation, upload and the execution entry
 // points.  Every step of the transform runs in the kernels of this library.
+#include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -87,6 +89,11 @@ namespace bfly_state {
 bfly_status set_error(bfly_status s, const std::string &msg) { return fail(s, msg); }
 }  // namespace bfly_state
 
+namespace {
+bfly_status autotune_create(bfly_plan_t *out, int dim, double N, int64_t nx, const double *x, int64_t nk,
+                            const double *k, int p, bfly_opts o);
+}
+
 extern "C" {
 
 const char *bfly_last_error(void) { return g_err.c_str(); }
@@ -129,8 +136,10 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   if (o.prec != BFLY_PREC_FP32 && o.prec != BFLY_PREC_FP64)
     return fail(BFLY_ERR_INVALID_ARG, "unknown precision");
   if (o.max_nrhs < 1 || o.max_nrhs > 4096) return fail(BFLY_ERR_INVALID_ARG, "max_nrhs must be in 1..4096");
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 2; ++i)
     if (o.reserved[i] != 0) return fail(BFLY_ERR_INVALID_ARG, "reserved options must be zero");
+  if ((o.flags & BFLY_FLAG_AUTOTUNE) && !(o.flags & BFLY_FLAG_HOST_ONLY))
+    return autotune_create(out, dim, N, nx, x, nk, k, p, o);
 
   bfly_plan_t P = new (std::nothrow) bfly_plan_s();
   if (!P) return fail(BFLY_ERR_OUT_OF_MEMORY, "host allocation");
@@ -354,6 +363,8 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     return fail(BFLY_ERR_UNSUPPORTED, msg);
   }
   P->level_grid = blocks * sms;
+  I.smem_kb = (int)((P->level_smem + 1023) / 1024);
+  I.blocks_per_sm = blocks;
   I.workspace_bytes = (int64_t)P->dbytes;
   I.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = P;
@@ -500,3 +511,121 @@ bfly_status bfly_plan_stage(bfly_plan_t plan, int t, int64_t *nA, int64_t *nB) {
 }
 
 }  // extern "C"
+
+namespace {
+
+// ---- autotuning of the recursive step (BFLY_FLAG_AUTOTUNE)
+
+std::string tune_key(int dim, int p, int prec, int nrhs, int64_t max_pairs) {
+  cudaDeviceProp prop{};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaGetDeviceProperties(&prop, dev);
+  std::string name = prop.name;
+  for (auto &ch : name)
+    if (ch == ' ') ch = '_';
+  int size_class = 0;  // log2 of the largest stage's pair count
+  while ((int64_t(1) << (size_class + 1)) <= max_pairs) ++size_class;
+  return name + " d" + std::to_string(dim) + " p" + std::to_string(p) + " prec" + std::to_string(prec) +
+         " nrhs" + std::to_string(nrhs) + " pairs2^" + std::to_string(size_class);
+}
+
+int cache_lookup(const char *path, const std::string &key) {
+  if (!path) return 0;
+  FILE *fh = std::fopen(path, "r");
+  if (!fh) return 0;
+  char line[512];
+  int found = 0;
+  while (std::fgets(line, sizeof line, fh)) {
+    std::string l(line);
+    const size_t sp = l.rfind(' ');
+    if (sp == std::string::npos) continue;
+    if (l.compare(0, sp, key) == 0) found = std::atoi(l.c_str() + sp + 1);
+  }
+  std::fclose(fh);
+  return found;
+}
+
+void cache_store(const char *path, const std::string &key, int smem_kb) {
+  if (!path) return;
+  FILE *fh = std::fopen(path, "a");
+  if (!fh) return;
+  std::fprintf(fh, "%s %d\n", key.c_str(), smem_kb);
+  std::fclose(fh);
+}
+
+// Time of one forward sweep (median of 3 after a warm-up) on the plan's staging buffers.
+bfly_status time_plan(bfly_plan_t P, double *ms) {
+  const int nrhs = P->max_nrhs;
+  const size_t bytes = (size_t)std::max(P->nx, P->nk) * 16 * nrhs;
+  BFLY_CUDA(cudaMemset(P->stage_in, 0, bytes));
+  cudaEvent_t e0, e1;
+  BFLY_CUDA(cudaEventCreate(&e0));
+  BFLY_CUDA(cudaEventCreate(&e1));
+  std::vector<float> t;
+  bfly_status st = BFLY_OK;
+  for (int r = 0; r < 4 && st == BFLY_OK; ++r) {
+    cudaEventRecord(e0, 0);
+    st = run(P, P->stage_in, P->stage_out, nrhs, BFLY_C64, false, 0);
+    cudaEventRecord(e1, 0);
+    cudaEventSynchronize(e1);
+    float v = 0;
+    cudaEventElapsedTime(&v, e0, e1);
+    if (r > 0) t.push_back(v);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != BFLY_OK) return st;
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  return BFLY_OK;
+}
+
+bfly_status autotune_create(bfly_plan_t *out, int dim, double N, int64_t nx, const double *x, int64_t nk,
+                            const double *k, int p, bfly_opts o) {
+  o.flags &= ~BFLY_FLAG_AUTOTUNE;
+  // a host-only plan first: the size class of the key
+  bfly_opts ho = o;
+  ho.flags |= BFLY_FLAG_HOST_ONLY;
+  bfly_plan_t H = nullptr;
+  bfly_status st = bfly_plan_create(&H, dim, N, nx, x, nk, k, p, &ho);
+  if (st != BFLY_OK) return st;
+  const std::string key = tune_key(dim, p, o.prec, o.max_nrhs, H->info.max_pairs);
+  bfly_plan_destroy(H);
+  const int cached = cache_lookup(o.tune_cache, key);
+  if (cached > 0) {
+    o.smem_kb = cached;
+    return bfly_plan_create(out, dim, N, nx, x, nk, k, p, &o);
+  }
+  const int candidates[] = {40, 55, 73, 110, 220};
+  bfly_plan_t best = nullptr;
+  double best_ms = 0;
+  int best_kb = 0;
+  for (int kb : candidates) {
+    bfly_opts c = o;
+    c.smem_kb = kb;
+    bfly_plan_t P = nullptr;
+    if (bfly_plan_create(&P, dim, N, nx, x, nk, k, p, &c) != BFLY_OK) continue;
+    double ms = 0;
+    if (time_plan(P, &ms) != BFLY_OK) {
+      bfly_plan_destroy(P);
+      continue;
+    }
+    if (!best || ms < best_ms) {
+      if (best) bfly_plan_destroy(best);
+      best = P;
+      best_ms = ms;
+      best_kb = kb;
+    } else {
+      bfly_plan_destroy(P);
+    }
+  }
+  if (!best) return fail(BFLY_ERR_UNSUPPORTED, "autotuning: no candidate configuration could be built");
+  best->info.tuned_ms = best_ms;
+  cache_store(o.tune_cache, key, best_kb);
+  g_err.clear();
+  *out = best;
+  return BFLY_OK;
+}
+
+}  // namespace

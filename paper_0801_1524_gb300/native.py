@@ -14,6 +14,7 @@ BFLY_C64, BFLY_C128 = 0, 1
 BFLY_PREC_FP64, BFLY_PREC_FP32 = 0, 1
 BFLY_FLAG_HOST_ONLY = 1
 BFLY_FLAG_TEST_STALL = 2
+BFLY_FLAG_AUTOTUNE = 4
 
 # Every function the header declares, with (restype, argtypes).
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -21,7 +22,8 @@ _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_doub
 
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("flags", ctypes.c_uint),
-                ("smem_kb", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("smem_kb", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -31,7 +33,9 @@ class PlanInfo(ctypes.Structure):
                 ("max_pairs", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("tiles_read_fwd", ctypes.c_int64), ("tiles_written_fwd", ctypes.c_int64),
                 ("jobs_fwd", ctypes.c_int64), ("chunks_fwd", ctypes.c_int64),
-                ("flops_fwd", ctypes.c_double), ("plan_seconds", ctypes.c_double)]
+                ("flops_fwd", ctypes.c_double), ("smem_kb", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int), ("tuned_ms", ctypes.c_double),
+                ("plan_seconds", ctypes.c_double)]
 
 
 SIGNATURES = {

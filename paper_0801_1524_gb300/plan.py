@@ -41,7 +41,8 @@ class Plan:
     """
 
     def __init__(self, x, k, N: float, p: int, precision: str = "fp32", max_nrhs: int = 1,
-                 host_only: bool = False, smem_kb: int = 0, flags: int = 0):
+                 host_only: bool = False, smem_kb: int = 0, flags: int = 0,
+                 autotune: bool = False, tune_cache: str | None = None):
         lib = native.load()
         x = np.ascontiguousarray(x, dtype=np.float64)
         k = np.ascontiguousarray(k, dtype=np.float64)
@@ -58,8 +59,11 @@ class Plan:
         opts = native.Opts()
         opts.prec = PRECISIONS[precision]
         opts.max_nrhs = self.max_nrhs
-        opts.flags = (native.BFLY_FLAG_HOST_ONLY if host_only else 0) | int(flags)
+        opts.flags = ((native.BFLY_FLAG_HOST_ONLY if host_only else 0) |
+                      (native.BFLY_FLAG_AUTOTUNE if autotune else 0) | int(flags))
         opts.smem_kb = int(smem_kb)
+        self._tune_cache = tune_cache.encode() if tune_cache else None
+        opts.tune_cache = self._tune_cache
         h = ctypes.c_void_p()
         self._lib = lib
         self._h = None
