@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--nrhs", type=int, default=16, help="right-hand sides (star_batch)")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--smem-kb", type=int, default=0,
+                    help="shared memory per block of the recursive step (0 = the library default)")
     return ap.parse_args()
 
 
@@ -155,6 +157,23 @@ def oracle_direct_rate(inst, f, seconds: float, seed: int = 12345):
     return (m / nx) / dt, m, threads(), dt
 
 
+# ---------------------------------------------------------------------------- ranks
+def max_over_ranks(ms, dist, device=None):
+    """The largest of every rank's step time, on every rank (the job's time: replicas
+    run independently, the slowest one bounds the whole job)."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, ms):
+    """Transforms per second of the whole job: one transform per rank per step."""
+    return world * 1e3 / ms
+
+
 # ---------------------------------------------------------------------------- main arm
 def main_bfly(args, rank, world, dist):
     import torch
@@ -168,7 +187,7 @@ def main_bfly(args, rank, world, dist):
     f_np = inst.sources(dtype=np.complex64)[0]
     stream = torch.cuda.current_stream()
     f = torch.as_tensor(f_np, device=dev)
-    plan = Plan(inst.x, inst.k, inst.N, inst.p, precision="fp32")
+    plan = Plan(inst.x, inst.k, inst.N, inst.p, precision="fp32", smem_kb=args.smem_kb)
     info = plan.info()
     L = info["L"]
     u = torch.empty(nx, dtype=torch.complex64, device=dev)
@@ -209,11 +228,7 @@ def main_bfly(args, rank, world, dist):
     step_ms = [ev[0].elapsed_time(ev[L + 2]) for ev in events]
     level_ms = [ev[1].elapsed_time(ev[L + 1]) for ev in events]
     kern_ms = np.array([[ev[i].elapsed_time(ev[i + 1]) for i in range(L + 2)] for ev in events])
-    ms = float(np.mean(step_ms))
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(step_ms)), dist, dev)
     clk = clocks.stop() if clocks else None
 
     # ---- end to end through the host-buffer C-ABI call (copies inside the timed call)
@@ -312,7 +327,7 @@ def main_bfly(args, rank, world, dist):
     kern_names = ["leaf"] + [f"level_t{t}" for t in range(L - 1, -1, -1)] + ["final"]
     out["kernel_ms"] = {n: float(v) for n, v in zip(kern_names, kern_ms.mean(axis=0))}
 
-    value = world * 1e3 / ms
+    value = replica_value(world, ms)
     line = {
         "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -386,8 +401,8 @@ def main_reference(args, rank):
 
 
 def main_batch(args):
-    """64 star-curve instances (N log-uniform in [512, 16384] rounded to powers of two),
-    p = 7, nrhs complex64 right-hand sides each, one graph replay per step."""
+    """64 star-curve instances (N log-uniform in [512, 16384], as drawn), p = 7, nrhs
+    complex64 right-hand sides each, one graph replay per step."""
     import torch
     from paper_0801_1524_gb300 import workloads as w
     from paper_0801_1524_gb300.plan import Batch, Plan
@@ -432,7 +447,7 @@ def main_batch(args):
     line = {"metric": METRIC + " (batched)", "value": len(insts) * args.nrhs * 1e3 / ms,
             "unit": "instance-RHS transforms/s", "ms_per_step": ms, "steps": args.steps,
             "warmup": args.warmup, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"star_batch: 64 instances, N in 512..16384 (powers of two), p=7, "
+            "config": {"workload": f"star_batch: 64 instances, N log-uniform in 512..16384, p=7, "
                                    f"{args.nrhs} complex64 RHS, graph replay",
                        "sum_N": float(sum(I.N for I in insts)),
                        "points": int(sum(I.x.shape[0] + I.k.shape[0] for I in insts))},

@@ -71,9 +71,10 @@ typedef struct {
 } bfly_opts;
 
 typedef struct {
-  int dim, p, L;                /* L = log2 N levels below the root */
+  int dim, p, L;                /* L = ceil(log2 N) levels below the root (0 if N <= 1) */
   int prec;                     /* bfly_precision of the plan */
   double N;
+  double rho;                   /* leaf width N / 2^L, in (1/2, 1]; 1 when N = 2^L */
   int64_t nx, nk;               /* number of targets and sources */
   int64_t total_pairs;          /* sum over stages t of nA(L-t) * nK(t) */
   int64_t max_pairs;            /* largest stage */
@@ -83,6 +84,8 @@ typedef struct {
   int64_t jobs_fwd;             /* (output box pair, child) pairs of the recursive step */
   int64_t chunks_fwd;           /* blocks of work of the recursive step, all stages */
   double flops_fwd;             /* real flops of the recursive step as executed, one RHS */
+  double lane_use_fwd;          /* recursive step: fraction of the issued lanes that work
+                                   (operator groups are processed 32 fibres at a time) */
   int smem_kb;                  /* shared-memory budget per block of the recursive step */
   int blocks_per_sm;            /* resident blocks of the recursive step per SM */
   double tuned_ms;              /* autotuning: time of the chosen candidate (0 if not tuned) */
@@ -91,19 +94,23 @@ typedef struct {
 
 /*
  * bfly_plan_create — Sec. 2.2 step 1 and everything that depends only on the points:
- * scales nothing (the points are already in [0,N]^dim), assigns every point to its unit
- * leaf box (index min(floor(x), N-1) per axis), sorts the points by leaf in Morton
- * order, builds the non-empty boxes of every level of T_X and T_K with their child
- * ranges, the transfer operators (eqs. M1 and E1 combined, built in FP64), and the
- * per-point interpolation weights of steps 2 and 4; uploads all of it and allocates two
- * charge buffers of the largest stage (Sec. 2.2: two adjacent levels are live).
+ * scales nothing (the points are already in [0,N]^dim), builds L = ceil(log2 N) levels
+ * below the root with leaves of width rho = N / 2^L (unit leaves when N is a power of
+ * two, the setting of Sec. 2.2; otherwise w^A w^B = rho N <= N, which keeps the rank
+ * bound of Theorem 2.1), assigns every point to its leaf (index min(floor(x / rho),
+ * 2^L - 1) per axis), sorts the points by leaf in Morton order, builds the non-empty
+ * boxes of every level of T_X and T_K with their child ranges, the transfer operators
+ * (eqs. M1 and E1 combined, built in FP64), and the per-point interpolation weights of
+ * steps 2 and 4; uploads all of it and allocates two charge buffers of the largest stage
+ * (Sec. 2.2: two adjacent levels are live).
  *   out      receives the plan; *out is NULL on failure.
- *   dim      2 or 3.   N: a power of two >= 1.   p: 3, 5, 7 or 9.
+ *   dim      2 or 3.   N: finite, > 0.   p: 3, 5, 7 or 9.
  *   x, k     host arrays [nx][dim] and [nk][dim], every coordinate finite and in [0,N];
  *            copied, the caller keeps ownership.  nx, nk >= 1.
  *   opts     NULL for defaults.
- * Errors: INVALID_ARG (any of the above), UNSUPPORTED (N not a power of two; a p or
- * precision whose workspace does not fit on chip), OUT_OF_MEMORY, CUDA.
+ * Errors: INVALID_ARG (any of the above), UNSUPPORTED (even p; N beyond 2^30 in 2D or
+ * 2^20 in 3D; a p or precision whose workspace does not fit on chip), OUT_OF_MEMORY,
+ * CUDA.
  * The device current at the call owns the plan's memory; execute on that device.
  */
 bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx,
@@ -204,8 +211,10 @@ bfly_status bfly_device_status(bfly_plan_t plan, int *flags);
  * launch of the recursive step per stage over the work of every plan.
  *
  * bfly_batch_create — plans: count device plans (the caller keeps ownership and must
- *   keep them alive while the batch exists).  Errors: INVALID_ARG (NULL, host-only plans,
- *   mixed dim / p / precision / device), OUT_OF_MEMORY, CUDA.
+ *   keep them alive while the batch exists).  The plans must have been created with the
+ *   same shared-memory budget (smem_kb); each keeps its own operators (its own N).
+ *   Errors: INVALID_ARG (NULL, host-only plans, mixed dim / p / precision / device /
+ *   tile capacities), UNSUPPORTED, OUT_OF_MEMORY, CUDA.
  * bfly_batch_execute — f[i] (device, [nrhs][nk_i]) -> u[i] (device, [nrhs][nx_i]) for
  *   every plan i, nrhs <= every plan's max_nrhs, asynchronous on `stream`.  On a
  *   non-default stream the launches are captured into a CUDA graph the first time and

@@ -74,13 +74,11 @@ struct Arena {
   }
 };
 
-bool is_pow2(double N, int *L) {
-  if (!(N >= 1.0) || !std::isfinite(N)) return false;
-  int e = 0;
-  const double m = std::frexp(N, &e);
-  if (m != 0.5) return false;
-  *L = e - 1;
-  return true;
+// Levels below the root: the smallest L with 2^L >= N (up to a relative 1e-12), 0 for
+// N <= 1; the leaves are rho = N / 2^L wide, rho = 1 exactly when N = 2^L.
+int levels_for(double N) {
+  if (!(N > 1.0)) return 0;
+  return (int)std::ceil(std::log2(N) - 1e-12);
 }
 
 }  // namespace
@@ -122,8 +120,7 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   if (p < 3 || p > 9) return fail(BFLY_ERR_INVALID_ARG, "p must be in 3..9");
   if (p % 2 == 0) return fail(BFLY_ERR_UNSUPPORTED, "this build has kernels for p = 3, 5, 7, 9");
   if (!std::isfinite(N) || !(N > 0)) return fail(BFLY_ERR_INVALID_ARG, "N must be finite and > 0");
-  int L = 0;
-  if (!is_pow2(N, &L)) return fail(BFLY_ERR_UNSUPPORTED, "N must be a power of two >= 1");
+  const int L = levels_for(N);
   if ((dim == 2 && L > 30) || (dim == 3 && L > 20))
     return fail(BFLY_ERR_UNSUPPORTED, "N too large for 64-bit Morton keys");
   if (nx < 1 || nk < 1 || nx > INT32_MAX / 2 || nk > INT32_MAX / 2)
@@ -147,13 +144,14 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   P->p = p;
   P->L = L;
   P->N = N;
+  P->rho = std::ldexp(N, -L);  // exact
   P->nx = nx;
   P->nk = nk;
   P->prec = o.prec;
   P->max_nrhs = o.max_nrhs;
   P->flags = o.flags;
-  std::string err = bfly::build_tree(P->TX, dim, L, nx, x);
-  if (err.empty()) err = bfly::build_tree(P->TK, dim, L, nk, k);
+  std::string err = bfly::build_tree(P->TX, dim, L, P->rho, nx, x);
+  if (err.empty()) err = bfly::build_tree(P->TK, dim, L, P->rho, nk, k);
   if (!err.empty()) {
     delete P;
     return fail(BFLY_ERR_INVALID_ARG, err);
@@ -176,6 +174,7 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   I.L = L;
   I.prec = o.prec;
   I.N = N;
+  I.rho = P->rho;
   I.nx = nx;
   I.nk = nk;
   I.total_pairs = tot;
@@ -208,16 +207,22 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   P->TS = P->ks->tile_stride;
   // capacities: the largest chunk that fits the shared-memory budget of one block
   const size_t want = (size_t)(o.smem_kb > 0 ? o.smem_kb : 55) * 1024;
-  auto caps_for = [&](size_t budget) {
-    ChunkCaps c{0, 0, 0};
+  // The tile capacities follow from the budget alone (so that plans of any N made with
+  // one budget can share a batched launch); a plan with N != 2^L then adds its output
+  // factors to the metadata slots, a little above the budget.
+  const bool scaled = P->rho != 1.0;
+  auto caps_for = [&](size_t budget, bool count_scalars) {
     for (int cap = 1024; cap >= 8; cap -= 8) {
-      c = ChunkCaps{cap, cap, cap, P->ks->meta_bytes(cap, cap, cap)};
-      if (P->ks->level_smem(c) <= budget) return c;
+      ChunkCaps c{cap, cap, cap, P->ks->meta_bytes(cap, cap, cap, count_scalars)};
+      if (P->ks->level_smem(c) <= budget) {
+        c.meta_bytes = P->ks->meta_bytes(cap, cap, cap, scaled);
+        if (P->ks->level_smem(c) <= max_smem) return c;
+      }
     }
     return ChunkCaps{0, 0, 0, 0};
   };
-  ChunkCaps caps = caps_for(std::min(want, max_smem));
-  if (caps.cap0 == 0) caps = caps_for(max_smem);
+  ChunkCaps caps = caps_for(std::min(want, max_smem), false);
+  if (caps.cap0 == 0) caps = caps_for(max_smem, true);
   if (caps.cap0 == 0) {
     delete P;
     return fail(BFLY_ERR_UNSUPPORTED, "charge tiles of this (dim, p, precision) do not fit in shared memory");
@@ -226,29 +231,47 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   P->level_smem = P->ks->level_smem(caps);
   P->progF.resize(L);
   P->progA.resize(L);
+  int64_t lanes_used_all = 0, lanes_issued_all = 0;
   for (int t = 0; t < L; ++t) {
     const auto &csAp = P->TX.cs[L - t - 1], &xidx = P->TX.idx[L - t];
     const auto &csB = P->TK.cs[t], &kidx = P->TK.idx[t + 1];
-    P->progF[t] = bfly::make_stage_program(dim, p, csAp, xidx, csB, kidx, false, caps);
-    P->progA[t] = bfly::make_stage_program(dim, p, csAp, xidx, csB, kidx, true, caps);
+    P->progF[t] = bfly::make_stage_program(dim, p, P->rho, csAp, xidx, csB, kidx, false, caps);
+    P->progA[t] = bfly::make_stage_program(dim, p, P->rho, csAp, xidx, csB, kidx, true, caps);
     for (int dir = 0; dir < 2; ++dir) {
       const int64_t tin = dir ? P->pairs[t] : P->pairs[t + 1], tout = dir ? P->pairs[t + 1] : P->pairs[t];
-      const std::string bad = bfly::validate_program(dir ? P->progA[t] : P->progF[t], dim, caps, tin, tout);
+      const std::string bad = bfly::validate_program(dir ? P->progA[t] : P->progF[t], dim, p, caps, tin, tout);
       if (!bad.empty()) {
         delete P;
         return fail(BFLY_ERR_CUDA, "internal error in the stage program: " + bad);
       }
     }
     I.chunks_fwd += (int64_t)P->progF[t].chunks.size();
-    int64_t srcs = 0;  // one task per (output tile of a pass, source)
+    int64_t lanes_used = 0, lanes_issued = 0;
+    int64_t srcs = 0;  // (output tile of a pass, source) pairs
     for (const auto &cd : P->progF[t].chunks) {
-      const int32_t *hdr = reinterpret_cast<const int32_t *>(P->progF[t].blob.data() + cd.blob_off);
-      for (int k = 0; k < dim; ++k) srcs += hdr[2 * k] + hdr[2 * k + 1];  // tasks of pass k
+      const unsigned char *bp = P->progF[t].blob.data() + cd.blob_off;
+      const int32_t *hdr = reinterpret_cast<const int32_t *>(bp);
+      int64_t ni = 0;
+      for (int k = 0; k < dim; ++k) ni += hdr[k];
+      const bfly::Item *it = reinterpret_cast<const bfly::Item *>(bp + bfly::kBlobHeader);
+      for (int64_t i = 0; i < ni; ++i) srcs += 1 + (it[i].src1 != 0xffff);
+      // lanes used by the steps of every operator group (32 fibres per step)
+      const bfly::Group *gr = reinterpret_cast<const bfly::Group *>(it + ni);
+      int64_t ng = 0;
+      for (int k = 0; k < dim; ++k) ng += hdr[3 + k];
+      for (int64_t g = 0; g < ng; ++g) {
+        const int64_t fibres = (int64_t)gr[g].n_items * (PD / p), w = gr[g].op1 == 0xffff ? 1 : 2;
+        lanes_used += fibres * w;
+        lanes_issued += (fibres + 31) / 32 * 32 * w;
+      }
     }
     double fib_p2 = 1.0;  // fibres x p^2 complex multiply-adds per source, 8 flops each
     for (int d = 0; d < dim + 1; ++d) fib_p2 *= p;
     I.flops_fwd += (double)srcs * fib_p2 * 8.0;
+    lanes_used_all += lanes_used;
+    lanes_issued_all += lanes_issued;
   }
+  I.lane_use_fwd = lanes_issued_all ? (double)lanes_used_all / (double)lanes_issued_all : 1.0;
   if (host_only) {
     I.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = P;
@@ -260,14 +283,14 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   for (int m = 0; m < p; ++m) {
     double den = 1.0;
     for (int n2 = 0; n2 < p; ++n2)
-      if (n2 != m) den *= std::sin(M_PI * (double)(m - n2) / ((double)q * q));
+      if (n2 != m) den *= std::sin(M_PI * P->rho * ((double)(m - n2) / ((double)q * q)));
     inv_den[m] = 1.0 / den;
   }
-  std::vector<double> tabF = bfly::transfer_table(p, false), tabH = bfly::transfer_table(p, true);
+  std::vector<double> tabF = bfly::transfer_table(p, P->rho, false), tabH = bfly::transfer_table(p, P->rho, true);
   // FP32 operators for the recursive step: [op][l][m], m padded to an even count
   std::vector<float> tabF32, tabH32;
   if (o.prec == BFLY_PREC_FP32) {
-    const int pp = (p + 1) & ~1, nops = 4 * q;
+    const int pp = (p + 1) & ~1, nops = 4;
     tabF32.assign((size_t)nops * p * pp * 2, 0.0f);
     tabH32.assign(tabF32.size(), 0.0f);
     for (int op = 0; op < nops; ++op)
@@ -289,7 +312,6 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   A.add_vec(&P->leaf_k, P->TK.leaf_start);
   A.add_vec(&P->pleaf_x, P->TX.point_leaf);
   A.add_vec(&P->pleaf_k, P->TK.point_leaf);
-  A.add_vec(&P->lidx_x, P->TX.idx[L]);
   A.add_vec(&P->off_x, P->TX.off);
   A.add_vec(&P->off_k, P->TK.off);
   A.add_vec(&P->xs, xs);
@@ -341,11 +363,11 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     at += (it.bytes + 255) & ~(size_t)255;
   }
   if (e == cudaSuccess)
-    e = bfly::launch_weights(o.prec == BFLY_PREC_FP64 ? 0 : 1, nk, dim, p, 0, P->off_k, P->pleaf_k,
-                             nullptr, P->inv_den, P->Wk, 0);
+    e = bfly::launch_weights(o.prec == BFLY_PREC_FP64 ? 0 : 1, nk, dim, p, P->rho, 0, P->off_k, P->inv_den,
+                             P->Wk, 0);
   if (e == cudaSuccess)
-    e = bfly::launch_weights(o.prec == BFLY_PREC_FP64 ? 0 : 1, nx, dim, p, 1, P->off_x, P->pleaf_x,
-                             P->lidx_x, P->inv_den, P->Wx, 0);
+    e = bfly::launch_weights(o.prec == BFLY_PREC_FP64 ? 0 : 1, nx, dim, p, P->rho, 1, P->off_x, P->inv_den,
+                             P->Wx, 0);
   int blocks = 0;
   if (e == cudaSuccess) e = P->ks->level_setup(P->level_smem, &blocks);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

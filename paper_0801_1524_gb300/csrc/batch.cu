@@ -1,5 +1,6 @@
 // Batched execution of many plans (independent transforms of uneven N and point counts,
-// each with nrhs right-hand sides): the leaf step of every plan, then one launch of the
+// each with nrhs right-hand sides; the plans share dim, p, precision and tile capacities,
+// each keeps its own operators): the leaf step of every plan, then one launch of the
 // recursive-step kernel per stage t = L_max-1 .. 0 over the chunks of every plan that
 // has that stage (plans are aligned at the final stage), then the final step of every
 // plan.  On a non-default stream the whole sequence is captured once into a CUDA graph
@@ -13,6 +14,8 @@
 
 struct bfly_batch_s {
   int count = 0, dim = 0, p = 0, prec = 0, L_max = 0, max_nrhs = 0, device = -1;
+  int meta_bytes = 0, grid = 0;  // the largest metadata slot of the plans; persistent blocks
+  size_t smem = 0;
   std::vector<bfly_plan_t> plans;
   char *dmem = nullptr;
   std::vector<bfly::BatchEntry *> entries;  // per stage t
@@ -50,7 +53,7 @@ bfly_status launch_all(bfly_batch_t B, const void *const *f, void *const *u, int
   bfly_plan_t P0 = B->plans[0];
   for (int t = B->L_max - 1; t >= 0; --t) {
     if (B->n_entries[t] == 0) continue;
-    // the operator table and capacities of plan 0 serve all (same dim, p, precision)
+    // the tile capacities of plan 0 serve all; every entry names its plan's operators
     bfly::LevelArgs a{};
     a.nrhs = nrhs;
     a.entries = B->entries[t];
@@ -58,10 +61,10 @@ bfly_status launch_all(bfly_batch_t B, const void *const *f, void *const *u, int
     a.table = P0->table;
     a.cap0 = P0->caps.cap0;
     a.cap1 = P0->caps.cap1;
-    a.meta_bytes = P0->caps.meta_bytes;
+    a.meta_bytes = B->meta_bytes;
     a.wait_limit = 2000000000LL;  // ~1 s of SM clock
     a.status = B->status;
-    BATCH_CUDA(P0->ks->level(a, false, P0->level_grid, P0->level_smem, s));
+    BATCH_CUDA(P0->ks->level(a, false, B->grid, B->smem, s));
   }
   for (int i = 0; i < B->count; ++i) {
     bfly_plan_t P = B->plans[i];
@@ -93,10 +96,20 @@ bfly_status bfly_batch_create(bfly_batch_t *out, int count, const bfly_plan_t *p
     if (!P || !P->dmem) return set_error(BFLY_ERR_INVALID_ARG, "every plan must be a device plan");
     if (P->dim != P0->dim || P->p != P0->p || P->prec != P0->prec || P->device != P0->device)
       return set_error(BFLY_ERR_INVALID_ARG, "plans of a batch share dim, p, precision and device");
-    if (P->level_smem != P0->level_smem || P->caps.cap0 != P0->caps.cap0 || P->caps.cap1 != P0->caps.cap1 ||
-        P->caps.meta_bytes != P0->caps.meta_bytes)
-      return set_error(BFLY_ERR_INVALID_ARG, "plans of a batch share their shared-memory configuration");
+    if (P->caps.cap0 != P0->caps.cap0 || P->caps.cap1 != P0->caps.cap1 || P->caps.max_out != P0->caps.max_out)
+      return set_error(BFLY_ERR_INVALID_ARG, "plans of a batch share their shared-memory tile capacities");
   }
+  // one launch serves every plan: metadata slots as large as the largest plan's
+  int meta = 0;
+  for (int i = 0; i < count; ++i) meta = std::max(meta, plans[i]->caps.meta_bytes);
+  bfly::ChunkCaps caps = P0->caps;
+  caps.meta_bytes = meta;
+  const size_t smem = P0->ks->level_smem(caps);
+  int blocks = 0, sms = 0;
+  cudaError_t es = P0->ks->level_setup(smem, &blocks);
+  if (es == cudaSuccess) es = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P0->device);
+  if (es != cudaSuccess) return set_error(BFLY_ERR_CUDA, std::string("batch setup: ") + cudaGetErrorString(es));
+  if (blocks < 1) return set_error(BFLY_ERR_UNSUPPORTED, "the batch's blocks do not fit in shared memory");
   bfly_batch_t B = new bfly_batch_s();
   B->count = count;
   B->dim = P0->dim;
@@ -105,6 +118,9 @@ bfly_status bfly_batch_create(bfly_batch_t *out, int count, const bfly_plan_t *p
   B->device = P0->device;
   B->plans.assign(plans, plans + count);
   B->max_nrhs = P0->max_nrhs;
+  B->meta_bytes = meta;
+  B->smem = smem;
+  B->grid = blocks * sms;
   for (auto *P : B->plans) {
     B->L_max = std::max(B->L_max, P->L);
     B->max_nrhs = std::min(B->max_nrhs, P->max_nrhs);
@@ -124,6 +140,8 @@ bfly_status bfly_batch_create(bfly_batch_t *out, int count, const bfly_plan_t *p
         e.out = P->buf[t & 1];
         e.in_rhs = P->pairs[t + 1] * P->TS;
         e.out_rhs = P->pairs[t] * P->TS;
+        e.table = P->table;
+        e.pad = 0;
         host[t].push_back(e);
       }
     }

@@ -17,13 +17,22 @@ struct Impl {
     return cudaGetLastError();
   }
   static cudaError_t level_setup(size_t smem, int *blocks) {
-    cudaError_t e = cudaFuncSetAttribute(level_kernel<R, D, P>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // The limit is a property of the kernel function, shared by every plan on the device:
+    // raise it to the device's opt-in maximum (never lower it to one plan's size, which
+    // would make launches of a plan with larger blocks fail).
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (smem > (size_t)optin) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(level_kernel<R, D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, level_kernel<R, D, P>, kLevelThreads, smem);
   }
   static size_t level_smem(const ChunkCaps &c) { return S::bytes(c); }
-  static int meta_bytes(int cap0, int cap1, int max_out) { return S::meta_bytes(cap0, cap1, max_out); }
+  static int meta_bytes(int cap0, int cap1, int max_out, bool scaled) {
+    return S::meta_bytes(cap0, cap1, max_out, scaled);
+  }
   static cudaError_t spread(const PointArgs &a, cudaStream_t s) {
     constexpr int PD = ipow(P, D);
     const int64_t work = a.nbox * PD;

@@ -17,12 +17,14 @@
 // output runs, cp.async.bulk shared -> global), waits until those stores have read the
 // slot, then copies chunk i's metadata blob and input tiles (runs of consecutive 16-byte
 // aligned tiles) into the slot with bulk copies completing on the slot's "full" mbarrier.
-// The consumer warps wait on "full" and run the passes.  A pass is two phases of tasks
-// (first sources: store; second sources: add), each grouped by operator; a group's
-// fibres are taken 32 at a time ("steps", one fibre per lane), a warp takes a contiguous
-// range of steps, loads each group's operator once into registers (the same operator in
-// every lane, so no divergence) and streams its fibres through it: P loads, P^2 complex
-// multiply-adds and P stores per fibre.  The last pass stages its tiles in the slot; the consumers then signal
+// The consumer warps wait on "full" and run the passes.  A pass's items are grouped by
+// their pair of operators (op0 for the first source, op1 for the second, if any); a
+// group's fibres are taken 32 at a time ("steps", one fibre per lane), the warps split
+// the pass's work (one unit per source of a step) evenly, and every lane of a step
+// computes y = T^{op0} x0 (+ T^{op1} x1) for its fibre with operator reads that are
+// broadcasts (the same operators in every lane, so no divergence): P or 2P loads, P^2 or
+// 2P^2 complex multiply-adds and P stores per fibre, one barrier per pass.  The last
+// pass stages its tiles in the slot; the consumers then signal
 // the slot's "staged" mbarrier and go on with the other slot, so that the write-back and
 // the next copies overlap their compute.  Every mbarrier wait gives up after a clock
 // budget, sets the status word and leaves the loop together with its peers; the producer
@@ -47,7 +49,7 @@ template <typename R, int D, int P>
 struct LevelShape {
   using C = typename Cx<R>::T;
   static constexpr int Q = P - 1;
-  static constexpr int NOPS = 4 * Q;
+  static constexpr int NOPS = 4;  // C^{(gamma, delta)}, op = gamma*2 + delta
   static constexpr int PD = ipow(P, D);
   static constexpr int TS = tile_stride<R>(PD);
   static constexpr int FIB = PD / P;  // fibres of one tile along one axis
@@ -57,10 +59,11 @@ struct LevelShape {
   static constexpr int OPS = sizeof(R) == 4 ? P * PP : P * P;  // elements per operator
   static constexpr size_t table_bytes = (size_t)NOPS * OPS * sizeof(C);
   static constexpr size_t tile_bytes = (size_t)TS * sizeof(C);
-  static int meta_bytes(int cap0, int cap1, int max_out) {
-    // at most two tasks and two operator groups per item, one run per output
+  static int meta_bytes(int cap0, int cap1, int max_out, bool scaled) {
+    // header, an item (8 bytes) and at most one operator group (12 bytes) per item, one
+    // run (8 bytes) and, for scaled programs, one FP64 complex factor per output, paddings
     const int items = cap1 + (D == 3 ? cap0 : 0) + max_out;
-    return (64 + 32 * items + 8 * max_out + 15) & ~15;
+    return (kBlobHeader + 20 * items + 8 * max_out + 8 + 15 + (scaled ? 16 * max_out : 0)) & ~15;
   }
   // table | 4 mbarriers | 2 metadata slots | 2 input buffers | scratch (2 in 3D, where
   // the last pass stages its outputs there)
@@ -145,81 +148,88 @@ __device__ __forceinline__ bool consumer_any(bool v) {
   return r != 0;
 }
 
-// One phase of pass K, warp `warp` of the consumers: for its steps (32 fibres of one
-// operator group, one per lane), y = T^{op} x along axis K, stored to (add = false) or
-// added to (add = true) the destination tile.
+// Accumulates y += T x for one fibre: x[l] = X[l * SK], T the operator at Tg (FP32:
+// transposed and padded, one 16-byte broadcast read gives T[m][l] and T[m+1][l]).
+template <typename R, int P, int PP, int SK>
+__device__ __forceinline__ void apply_op(const typename Cx<R>::T *Tg, const typename Cx<R>::T *X,
+                                         typename Cx<R>::T (&y)[P]) {
+  using C = typename Cx<R>::T;
+  C x[P];
+#pragma unroll
+  for (int l = 0; l < P; ++l) x[l] = X[l * SK];
+  // l outer, m inner: P independent multiply-add chains in flight
+#pragma unroll
+  for (int l = 0; l < P; ++l) {
+    if (sizeof(R) == 4) {
+      const float4 *Tl = reinterpret_cast<const float4 *>(Tg + l * PP);
+#pragma unroll
+      for (int m = 0; m < P; m += 2) {
+        const float4 t2 = Tl[m / 2];
+        y[m] = cfma(cmk((R)t2.x, (R)t2.y), x[l], y[m]);
+        if (m + 1 < P) y[m + 1] = cfma(cmk((R)t2.z, (R)t2.w), x[l], y[m + 1]);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < P; ++m) y[m] = cfma(Tg[m * P + l], x[l], y[m]);
+    }
+  }
+}
+
+// Pass K, warp `warp` of the consumers: for its steps (32 fibres of one operator group,
+// one per lane), y = T^{op0} x0 (+ T^{op1} x1) along axis K, stored to the item's
+// destination tile.  Every destination of a pass is written by exactly one item.
 template <typename R, int D, int P, int K>
-__device__ __forceinline__ void run_phase(const Task *tasks, const Group *groups, int ng,
-                                          const typename Cx<R>::T *src, typename Cx<R>::T *dst,
-                                          bool add, const typename Cx<R>::T *table, int warp,
-                                          int lane) {
+__device__ __forceinline__ void run_pass(const Item *items, const Group *groups, int ng,
+                                         const typename Cx<R>::T *src, typename Cx<R>::T *dst,
+                                         const typename Cx<R>::T *table, const double2 *scale,
+                                         int warp, int lane) {
   using C = typename Cx<R>::T;
   using S = LevelShape<R, D, P>;
   constexpr int FIB = S::FIB, TS = S::TS;
   constexpr int SK = ipow(P, D - 1 - K);  // element stride of axis K
   if (ng <= 0) return;
   const Group last = groups[ng - 1];
-  const int nsteps = last.step_begin + (last.n_tasks * FIB + 31) / 32;
-  const int per = (nsteps + kConsumerWarps - 1) / kConsumerWarps;
-  const int s0 = warp * per, s1 = min(nsteps, s0 + per);
-  if (s0 >= s1) return;
+  const int total = last.work_begin + ((last.n_items * FIB + 31) / 32) * (last.op1 == 0xffff ? 1 : 2);
+  const int per = (total + kConsumerWarps - 1) / kConsumerWarps;
+  const int w0 = warp * per, w1 = min(total, w0 + per);
+  if (w0 >= w1) return;
   int g = 0;
-  while (g + 1 < ng && groups[g + 1].step_begin <= s0) ++g;
+  while (g + 1 < ng && groups[g + 1].work_begin <= w0) ++g;
 #pragma unroll 1
   for (; g < ng; ++g) {
     const Group gr = groups[g];
-    if (gr.step_begin >= s1) break;
-    const int nfib = gr.n_tasks * FIB;
-    const int a = max(s0, (int)gr.step_begin), b = min(s1, gr.step_begin + (nfib + 31) / 32);
-    // the group's operator, the same in every lane: its reads are broadcasts
-    const C *Tg = table + (size_t)gr.op * S::OPS;
+    if (gr.work_begin >= w1) break;
+    const bool two = gr.op1 != 0xffff;
+    const int wt = two ? 2 : 1;
+    const int nfib = gr.n_items * FIB;
+    // steps j of the group whose work start work_begin + j * wt lies in [w0, w1)
+    const int a = w0 > gr.work_begin ? (w0 - gr.work_begin + wt - 1) / wt : 0;
+    const int b = min((nfib + 31) / 32, (w1 - gr.work_begin + wt - 1) / wt);
+    const C *T0 = table + (size_t)gr.op0 * S::OPS;
+    const C *T1 = table + (size_t)(two ? gr.op1 : gr.op0) * S::OPS;
 #pragma unroll 1
     for (int st = a; st < b; ++st) {
-      const int fl = (st - gr.step_begin) * 32 + lane;
+      const int fl = st * 32 + lane;
       if (fl >= nfib) continue;
       const int ti = fl / FIB, f = fl - ti * FIB;
-      const Task tk = tasks[gr.task_begin + ti];
+      const Item it = items[gr.item_begin + ti];
       const int base = (f / SK) * SK * P + (f % SK);
-      const C *X = src + (size_t)tk.src * TS + base;
-      C x[P];
-#pragma unroll
-      for (int l = 0; l < P; ++l) x[l] = X[l * SK];
-      C *Y = dst + (size_t)tk.dst * TS + base;
       C y[P];
 #pragma unroll
-      for (int m = 0; m < P; ++m) y[m] = add ? Y[m * SK] : cmk((R)0, (R)0);
-      // l outer, m inner: 2P independent multiply-add chains in flight
+      for (int m = 0; m < P; ++m) y[m] = cmk((R)0, (R)0);
+      apply_op<R, P, S::PP, SK>(T0, src + (size_t)it.src0 * TS + base, y);
+      if (two) apply_op<R, P, S::PP, SK>(T1, src + (size_t)it.src1 * TS + base, y);
+      if (K == D - 1 && scale) {  // the output tile's unit-modulus factor (N != 2^L)
+        const double2 sv = scale[it.dst];
+        const C sc = cmk((R)sv.x, (R)sv.y);
 #pragma unroll
-      for (int l = 0; l < P; ++l) {
-        if (sizeof(R) == 4) {
-          const float4 *Tl = reinterpret_cast<const float4 *>(Tg + l * S::PP);
-#pragma unroll
-          for (int m = 0; m < P; m += 2) {
-            const float4 t2 = Tl[m / 2];
-            y[m] = cfma(cmk((R)t2.x, (R)t2.y), x[l], y[m]);
-            if (m + 1 < P) y[m + 1] = cfma(cmk((R)t2.z, (R)t2.w), x[l], y[m + 1]);
-          }
-        } else {
-#pragma unroll
-          for (int m = 0; m < P; ++m) y[m] = cfma(Tg[m * P + l], x[l], y[m]);
-        }
+        for (int m = 0; m < P; ++m) y[m] = cmul(y[m], sc);
       }
+      C *Y = dst + (size_t)it.dst * TS + base;
 #pragma unroll
       for (int m = 0; m < P; ++m) Y[m * SK] = y[m];
     }
   }
-}
-
-// Pass K: phase 0 (first sources, store), then phase 1 (second sources, add).
-template <typename R, int D, int P, int K>
-__device__ __forceinline__ void run_pass(const Task *tasks, const int32_t *hdr, const Group *groups,
-                                         const typename Cx<R>::T *src, typename Cx<R>::T *dst,
-                                         const typename Cx<R>::T *table, int warp, int lane) {
-  const int n0 = hdr[2 * K], g0 = hdr[6 + 2 * K], g1 = hdr[6 + 2 * K + 1];
-  run_phase<R, D, P, K>(tasks, groups, g0, src, dst, false, table, warp, lane);
-  consumer_sync();
-  if (g1 > 0) run_phase<R, D, P, K>(tasks + n0, groups + g0, g1, src, dst, true, table, warp, lane);
-  consumer_sync();
 }
 
 template <typename R, int D, int P>
@@ -269,14 +279,14 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
       if (!__all_sync(0xffffffffu, ok)) return false;
       const unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
       const int32_t *hdr = reinterpret_cast<const int32_t *>(meta_s);
-      int n_tasks = 0, n_groups = 0;
+      int n_items = 0, n_groups = 0;
       for (int k = 0; k < D; ++k) {
-        n_tasks += hdr[2 * k] + hdr[2 * k + 1];
-        n_groups += hdr[6 + 2 * k] + hdr[6 + 2 * k + 1];
+        n_items += hdr[k];
+        n_groups += hdr[3 + k];
       }
-      const int n_oruns = hdr[13];
-      const Run *oruns = reinterpret_cast<const Run *>(meta_s + 64 + (size_t)n_tasks * sizeof(Task) +
-                                                       (size_t)n_groups * sizeof(Group));
+      const int n_oruns = hdr[7];
+      const Run *oruns = reinterpret_cast<const Run *>(meta_s + kBlobHeader + (size_t)n_items * sizeof(Item) +
+                                                       (((size_t)n_groups * sizeof(Group) + 7) & ~(size_t)7));
       const C *stage_t = D == 3 ? scr0 + (size_t)(s % S::NSCR) * a.cap1 * TS : slot0 + (size_t)s * a.cap0 * TS;
       const unsigned char *stage = reinterpret_cast<const unsigned char *>(stage_t);
       unsigned char *obase = gout;
@@ -340,6 +350,7 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
   }
 
   // ---------------- consumer warps
+  const void *cur_table = a.table;  // operators now in s_table
   for (int it = 0; it < n_work; ++it) {
     const int s = it & 1, use = it >> 1;
     const bool ok = mbar_wait(&full[s], use & 1, a.wait_limit);
@@ -351,20 +362,36 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
     C *in_s = slot0 + (size_t)s * a.cap0 * TS;
     C *scr = scr0 + (size_t)(s % S::NSCR) * a.cap1 * TS;
     const int32_t *hdr = reinterpret_cast<const int32_t *>(meta_s);
-    int n_tasks = 0;
-    for (int k = 0; k < D; ++k) n_tasks += hdr[2 * k] + hdr[2 * k + 1];
-    const Task *t0 = reinterpret_cast<const Task *>(meta_s + 64);
-    const Group *g0 = reinterpret_cast<const Group *>(t0 + n_tasks);
-    const Task *t1 = t0 + hdr[0] + hdr[1];
-    const Group *g1 = g0 + hdr[6] + hdr[7];
-    run_pass<R, D, P, 0>(t0, hdr, g0, in_s, scr, s_table, warp, lane);
+    const int n_items = hdr[0] + hdr[1] + hdr[2], n_groups = hdr[3] + hdr[4] + hdr[5];
+    const Item *i0 = reinterpret_cast<const Item *>(meta_s + kBlobHeader);
+    const Group *g0 = reinterpret_cast<const Group *>(i0 + n_items);
+    const Item *i1 = i0 + hdr[0];
+    const Group *g1 = g0 + hdr[3];
+    const double2 *scale = nullptr;
+    if (hdr[8]) {
+      const size_t soff = (kBlobHeader + (size_t)n_items * sizeof(Item) +
+                           (((size_t)n_groups * sizeof(Group) + 7) & ~(size_t)7) + (size_t)hdr[7] * sizeof(Run) + 15) &
+                          ~(size_t)15;
+      scale = reinterpret_cast<const double2 *>(meta_s + soff);
+    }
+    if (a.entries) {
+      // a batched launch: the chunk's plan may have its own operators (its own N)
+      const void *tb = a.entries[blockIdx.x + (it / a.nrhs) * gridDim.x].table;
+      if (tb != cur_table) {
+        const C *src = reinterpret_cast<const C *>(tb);
+        for (int e = tid; e < NOPS * S::OPS; e += kConsumerWarps * 32) s_table[e] = src[e];
+        cur_table = tb;
+        consumer_sync();
+      }
+    }
+    run_pass<R, D, P, 0>(i0, g0, hdr[3], in_s, scr, s_table, scale, warp, lane);
+    consumer_sync();
     if (D == 3) {
-      const Task *t2 = t1 + hdr[2] + hdr[3];
-      const Group *g2 = g1 + hdr[8] + hdr[9];
-      run_pass<R, D, P, (D == 3 ? 1 : 0)>(t1, hdr, g1, scr, in_s, s_table, warp, lane);
-      run_pass<R, D, P, D - 1>(t2, hdr, g2, in_s, scr, s_table, warp, lane);  // staged in scr
+      run_pass<R, D, P, (D == 3 ? 1 : 0)>(i1, g1, hdr[4], scr, in_s, s_table, scale, warp, lane);
+      consumer_sync();
+      run_pass<R, D, P, D - 1>(i1 + hdr[1], g1 + hdr[4], hdr[5], in_s, scr, s_table, scale, warp, lane);  // staged in scr
     } else {
-      run_pass<R, D, P, D - 1>(t1, hdr, g1, scr, in_s, s_table, warp, lane);  // staged in in_s
+      run_pass<R, D, P, D - 1>(i1, g1, hdr[4], scr, in_s, s_table, scale, warp, lane);  // staged in in_s
     }
     fence_async_shared();  // the staged tiles are visible to the bulk stores
     consumer_sync();

@@ -17,12 +17,10 @@ inline uint64_t morton(const int64_t *a, int dim, int L) {
   return key;
 }
 
-// sin(pi * num / den) and cos(pi * num / den) for an exact rational angle.
-inline double sinpi_rat(double num, double den) { return std::sin(M_PI * (num / den)); }
 
 }  // namespace
 
-std::string build_tree(HostTree &T, int dim, int L, int64_t n, const double *pts) {
+std::string build_tree(HostTree &T, int dim, int L, double rho, int64_t n, const double *pts) {
   T = HostTree();
   T.dim = dim;
   T.L = L;
@@ -34,11 +32,12 @@ std::string build_tree(HostTree &T, int dim, int L, int64_t n, const double *pts
   for (int64_t i = 0; i < n; ++i) {
     for (int d = 0; d < dim; ++d) {
       const double v = pts[i * dim + d];
-      if (!(v >= 0.0) || !(v <= (double)side)) return "point coordinate outside [0, N]";
-      int64_t a = (int64_t)std::floor(v);
+      if (!(v >= 0.0) || !(v <= rho * (double)side)) return "point coordinate outside [0, N]";
+      const double u = v / rho;  // in leaf widths; exactly v when N = 2^L
+      int64_t a = (int64_t)std::floor(u);
       if (a > side - 1) a = side - 1;  // the far edge N belongs to the last box
       leaf[i * dim + d] = a;
-      off[i * dim + d] = v - (double)a;  // exact: v and a differ by less than 2
+      off[i * dim + d] = u - (double)a;  // exact: u and a differ by less than 2
     }
     key[i] = morton(&leaf[i * dim], dim, L);
   }
@@ -81,54 +80,52 @@ std::string build_tree(HostTree &T, int dim, int L, int64_t n, const double *pts
   return "";
 }
 
-void leaf_weights(int p, double tau, double *w) {
-  // G_{ll'} = exp(2 pi i l l'/q^2) is the Vandermonde matrix of the nodes
-  // z_m = exp(2 pi i m/q^2) and v(tau)_l = z(tau)^l with z(tau) = exp(2 pi i tau/q), so
-  // G^{-1} v(tau) holds the Lagrange basis polynomials of those nodes at z(tau).  As
+void leaf_weights(int p, double rho, double tau, double *w) {
+  // G_{ll'} = exp(2 pi i rho l l'/q^2) is the Vandermonde matrix of the nodes
+  // z_m = exp(2 pi i rho m/q^2) and v(tau)_l = z(tau)^l with z(tau) = exp(2 pi i rho tau/q),
+  // so G^{-1} v(tau) holds the Lagrange basis polynomials of those nodes at z(tau).  As
   // z - z_n = 2i sin((theta - phi_n)/2) e^{i(theta + phi_n)/2}, the product form is
-  //   w_m = e^{i pi (tau - m/q)} prod_{n != m} sin(pi (tau - n/q)/q) / sin(pi (m-n)/q^2),
+  //   w_m = e^{i pi rho (tau - m/q)} prod_{n != m} sin(pi rho (tau - n/q)/q) / sin(pi rho (m-n)/q^2),
   // which needs no inverse of the ill-conditioned G.
   const int q = p - 1;
   for (int m = 0; m < p; ++m) {
     double num = 1.0, den = 1.0;
     for (int n = 0; n < p; ++n) {
       if (n == m) continue;
-      num *= std::sin(M_PI * (tau - (double)n / q) / q);
-      den *= sinpi_rat((double)(m - n), (double)q * q);
+      num *= std::sin(M_PI * rho * (tau - (double)n / q) / q);
+      den *= std::sin(M_PI * rho * ((double)(m - n) / ((double)q * q)));
     }
-    const double ang = M_PI * (tau - (double)m / q);
+    const double ang = M_PI * rho * (tau - (double)m / q);
     w[2 * m] = std::cos(ang) * num / den;
     w[2 * m + 1] = std::sin(ang) * num / den;
   }
 }
 
-std::vector<double> transfer_table(int p, bool adjoint) {
-  // For A at level s with index a, w^A w^B = N, parent charges on the grid of B and
-  // child charges on the grid of Bc (child offset bit delta), the matching condition of
-  // Sec. 2.1 with the evaluation of Fig. 1 gives, per axis, f^{AB} = T f^{A'Bc} with
-  //   T_{m l} = omega^{-a m} e^{2 pi i a tau_l} w_m(tau_l),  tau_l = (delta + l/q)/2,
-  // omega = e^{2 pi i/q}: the Lagrange weights of the child grid point tau_l on the
-  // parent grid, times the box phases of eqs. M1 and E1 (the index of B cancels).  T
-  // depends on a only through alpha = a mod 2q.
+std::vector<double> transfer_table(int p, double rho, bool adjoint) {
+  // Per axis, for A (index a, width w^A) and B (width w^B) with w^A w^B = rho N, the
+  // matching condition of Sec. 2.1 with the evaluation of Fig. 1 gives f^{AB} = T f^{A'Bc},
+  //   T_{ml} = e^{-2 pi i rho a m/q} w_m(tau_l) e^{2 pi i rho a tau_l},  tau_l = (delta + l/q)/2
+  // (the index of B cancels; eqs. M1 and E1).  With the rescaled charges
+  // g^{AB}_m = e^{2 pi i rho a m/q} f^{AB}_m and a = 2a' + gamma this becomes
+  //   g^{AB} = e^{2 pi i rho a' delta} C(gamma, delta) g^{A'Bc},
+  //   C(gamma, delta)_{ml} = w_m(tau_l) e^{2 pi i rho gamma tau_l},
+  // four operators per axis whatever the level; the scalar is 1 when N = 2^L (rho = 1)
+  // and is applied per tile otherwise (make_stage_program).  Operator gamma*2 + delta.
   const int q = p - 1;
-  const int nops = 4 * q;
-  std::vector<double> T((size_t)nops * p * p * 2, 0.0);
+  std::vector<double> T((size_t)4 * p * p * 2, 0.0);
   std::vector<double> w((size_t)2 * p);
-  for (int alpha = 0; alpha < 2 * q; ++alpha) {
+  for (int gamma = 0; gamma < 2; ++gamma) {
     for (int delta = 0; delta < 2; ++delta) {
-      const int op = alpha * 2 + delta;
+      const int op = gamma * 2 + delta;
       for (int l = 0; l < p; ++l) {
         const double tau = (double)(delta * q + l) / (2.0 * q);
-        leaf_weights(p, tau, w.data());
-        // e^{2 pi i alpha tau} = e^{i pi (alpha (delta q + l) mod 2q)/q}
-        const int n1 = (alpha * (delta * q + l)) % (2 * q);
+        leaf_weights(p, rho, tau, w.data());
+        // e^{2 pi i rho gamma tau_l}: an exact rational angle when rho = 1
+        const double ang = rho == 1.0 ? M_PI * (double)(gamma * (delta * q + l)) / q : 2.0 * M_PI * rho * gamma * tau;
+        const double c = std::cos(ang), sn = std::sin(ang);
         for (int m = 0; m < p; ++m) {
-          // omega^{-alpha m} = e^{-i pi 2 (alpha m mod q)/q}
-          const int n2 = (2 * ((alpha * m) % q)) % (2 * q);
-          const int nn = ((n1 - n2) % (2 * q) + 2 * q) % (2 * q);
-          const double c = std::cos(M_PI * nn / q), s = std::sin(M_PI * nn / q);
           const double wr = w[2 * m], wi = w[2 * m + 1];
-          const double re = c * wr - s * wi, im = c * wi + s * wr;
+          const double re = c * wr - sn * wi, im = c * wi + sn * wr;
           const size_t at = adjoint ? (((size_t)op * p + l) * p + m) : (((size_t)op * p + m) * p + l);
           T[2 * at] = re;
           T[2 * at + 1] = adjoint ? -im : im;
@@ -153,16 +150,17 @@ struct UnitProg {
   int src[3][8][2];
   int op[3][8][2];
   int32_t out_tile[8];
+  double out_scale[8][2];  // unit-modulus factor of every output tile (rho != 1)
 };
 
 }  // namespace
 
-StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp,
+StageProgram make_stage_program(int dim, int p, double rho, const std::vector<int32_t> &csAp,
                                 const std::vector<int32_t> &xidx, const std::vector<int32_t> &csB,
                                 const std::vector<int32_t> &kidx, bool adjoint, ChunkCaps caps) {
   StageProgram prog;
-  const int q = p - 1;
   const int D = dim;
+  const bool scaled = rho != 1.0;
   const int64_t nAp = (int64_t)csAp.size() - 1, nB = (int64_t)csB.size() - 1;
   const int64_t nBc = (int64_t)kidx.size() / dim;
   const int64_t in_row = adjoint ? nB : nBc, out_row = adjoint ? nBc : nB;
@@ -215,49 +213,65 @@ StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp
       for (int v = 0; v < units[u].n_pass[D - 1]; ++v) outs.push_back(units[u].out_tile[v]);
     std::vector<int32_t> osorted = outs;
     std::sort(osorted.begin(), osorted.end());
-    std::vector<Task> tasks;
+    std::vector<Item> items;
     std::vector<Group> groups;
-    int32_t counts[6] = {0, 0, 0, 0, 0, 0}, gcounts[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<double> oscale(scaled ? 2 * osorted.size() : 0);
+    int32_t icount[3] = {0, 0, 0}, gcount[3] = {0, 0, 0};
     int fib = 1;  // fibres of one tile along one axis
     for (int d = 0; d + 1 < D; ++d) fib *= p;
     int oi = 0;
     for (int k = 0; k < D; ++k) {
-      std::vector<Task> ph[2];
+      struct Keyed {
+        uint16_t op0, op1;
+        Item it;
+      };
+      std::vector<Keyed> pass;
       for (size_t u = 0; u < units.size(); ++u) {
         const UnitProg &U = units[u];
         for (int v = 0; v < U.n_pass[k]; ++v) {
-          uint16_t dst;
+          Keyed e{0, 0xffff, Item{0xffff, 0xffff, 0, 0}};
           if (k == D - 1) {
             const int32_t g = outs[oi++];
-            dst = (uint16_t)(std::lower_bound(osorted.begin(), osorted.end(), g) - osorted.begin());
+            e.it.dst = (uint16_t)(std::lower_bound(osorted.begin(), osorted.end(), g) - osorted.begin());
+            if (scaled) {
+              oscale[2 * e.it.dst] = U.out_scale[v][0];
+              oscale[2 * e.it.dst + 1] = U.out_scale[v][1];
+            }
           } else {
-            dst = (uint16_t)(base[k][u] + v);
+            e.it.dst = (uint16_t)(base[k][u] + v);
           }
           int got = 0;
           for (int j = 0; j < 2; ++j) {
             const int sidx = U.src[k][v][j];
             if (sidx < 0) continue;
-            const int slot = k == 0 ? slot_of[base_in[u] + sidx] : base[k - 1][u] + sidx;
-            ph[got].push_back(Task{(uint16_t)slot, dst, (uint16_t)U.op[k][v][j], 0});
+            const uint16_t slot = (uint16_t)(k == 0 ? slot_of[base_in[u] + sidx] : base[k - 1][u] + sidx);
+            if (got == 0) {
+              e.it.src0 = slot;
+              e.op0 = (uint16_t)U.op[k][v][j];
+            } else {
+              e.it.src1 = slot;
+              e.op1 = (uint16_t)U.op[k][v][j];
+            }
             ++got;
           }
+          pass.push_back(e);
         }
       }
-      for (int f = 0; f < 2; ++f) {
-        std::stable_sort(ph[f].begin(), ph[f].end(), [](const Task &x, const Task &y) { return x.op < y.op; });
-        counts[2 * k + f] = (int32_t)ph[f].size();
-        int steps = 0;
-        for (size_t i = 0; i < ph[f].size();) {
-          size_t j = i;
-          while (j < ph[f].size() && ph[f][j].op == ph[f][i].op) ++j;
-          const int n = (int)(j - i);
-          groups.push_back(Group{(uint16_t)i, (uint16_t)n, ph[f][i].op, (uint16_t)steps});
-          steps += (n * fib + 31) / 32;
-          ++gcounts[2 * k + f];
-          i = j;
-        }
-        tasks.insert(tasks.end(), ph[f].begin(), ph[f].end());
+      std::stable_sort(pass.begin(), pass.end(), [](const Keyed &x, const Keyed &y) {
+        return x.op0 != y.op0 ? x.op0 < y.op0 : x.op1 < y.op1;
+      });
+      icount[k] = (int32_t)pass.size();
+      int work = 0;
+      for (size_t i = 0; i < pass.size();) {
+        size_t j = i;
+        while (j < pass.size() && pass[j].op0 == pass[i].op0 && pass[j].op1 == pass[i].op1) ++j;
+        const int n = (int)(j - i);
+        groups.push_back(Group{(uint16_t)i, (uint16_t)n, pass[i].op0, pass[i].op1, (uint16_t)work, 0});
+        work += ((n * fib + 31) / 32) * (pass[i].op1 == 0xffff ? 1 : 2);
+        ++gcount[k];
+        i = j;
       }
+      for (const Keyed &e : pass) items.push_back(e.it);
     }
     std::vector<Run> oruns;
     for (size_t r = 0; r < osorted.size(); ++r) {
@@ -267,22 +281,20 @@ StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp
         oruns.push_back(Run{osorted[r], (uint16_t)r, 1});
     }
     cur.blob_off = (int32_t)prog.blob.size();
-    int32_t header[16] = {0};
-    for (int i = 0; i < 6; ++i) {
-      header[i] = counts[i];
-      header[6 + i] = gcounts[i];
-    }
-    header[12] = cur.n_in;
-    header[13] = (int32_t)oruns.size();
-    const size_t ib = tasks.size() * sizeof(Task), gb = groups.size() * sizeof(Group);
+    const int32_t header[12] = {icount[0], icount[1], icount[2], gcount[0], gcount[1], gcount[2],
+                                cur.n_in, (int32_t)oruns.size(), scaled ? 1 : 0, 0, 0, 0};
+    const size_t ib = items.size() * sizeof(Item), gb = groups.size() * sizeof(Group);
     const size_t ob = oruns.size() * sizeof(Run);
-    const size_t bytes = (64 + ib + gb + ob + 15) & ~(size_t)15;
+    const size_t gpad = (gb + 7) & ~(size_t)7;  // runs start 8-byte aligned
+    const size_t soff = (kBlobHeader + ib + gpad + ob + 15) & ~(size_t)15;  // scalars 16-byte aligned
+    const size_t bytes = soff + oscale.size() * sizeof(double);
     prog.blob.resize(prog.blob.size() + bytes, 0);
     unsigned char *dstp = prog.blob.data() + cur.blob_off;
-    std::memcpy(dstp, header, 64);
-    std::memcpy(dstp + 64, tasks.data(), ib);
-    std::memcpy(dstp + 64 + ib, groups.data(), gb);
-    std::memcpy(dstp + 64 + ib + gb, oruns.data(), ob);
+    std::memcpy(dstp, header, kBlobHeader);
+    std::memcpy(dstp + kBlobHeader, items.data(), ib);
+    std::memcpy(dstp + kBlobHeader + ib, groups.data(), gb);
+    std::memcpy(dstp + kBlobHeader + ib + gpad, oruns.data(), ob);
+    if (scaled) std::memcpy(dstp + soff, oscale.data(), oscale.size() * sizeof(double));
     cur.blob_bytes = (int32_t)bytes;
     prog.chunks.push_back(cur);
     units.clear();
@@ -294,7 +306,6 @@ StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp
     const int a0 = csAp[iAp], a1 = csAp[iAp + 1];
     int apar[3] = {0, 0, 0};
     for (int d = 0; d < D; ++d) apar[d] = xidx[(int64_t)a0 * D + d] >> 1;
-    auto alpha = [&](int d, int bit) { return (2 * apar[d] + bit) % (2 * q); };
     for (int64_t iB = 0; iB < nB; ++iB) {
       const int c0 = csB[iB], c1 = csB[iB + 1];
       UnitProg U;
@@ -346,25 +357,46 @@ StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp
                 if (U.key[k - 1][j] == S) found = j;
             }
             U.src[k][v][b] = found;
-            // forward: alpha from the output (gamma) bit, delta = b; adjoint: alpha from
-            // the input (gamma) bit b, delta = the output bit
-            U.op[k][v][b] = adjoint ? alpha(k, b) * 2 + obit : alpha(k, obit) * 2 + b;
+            // operator gamma*2 + delta: forward, gamma is the output (A) bit and delta = b;
+            // adjoint, gamma is the input (A) bit b and delta the output (Bc) bit
+            U.op[k][v][b] = adjoint ? b * 2 + obit : obit * 2 + b;
           }
         }
       }
       for (int v = 0; v < U.n_pass[D - 1]; ++v) {
         // the last pass's keys are output keys: find that output's tile
         for (int o = 0; o < n_out; ++o)
-          if (okey[o] == U.key[D - 1][v])
+          if (okey[o] == U.key[D - 1][v]) {
             U.out_tile[v] = adjoint ? (int32_t)(iAp * out_row + dtile[o])
                                     : (int32_t)((int64_t)gtile[o] * out_row + iB);
+            if (scaled) {
+              // The factor e^{2 pi i rho a' delta} of the next stage belongs to its input
+              // tile (A', Bc), i.e. to this stage's output (A, B) with a' = a and delta the
+              // bit of B within its parent: forward, e^{2 pi i rho sum_d a_d beta_d(B)} on
+              // the output; adjoint, the conjugate of this stage's own factor on its
+              // output (A', Bc).  Phase rho * S reduced mod 1 in FP64.
+              int64_t S = 0;
+              for (int d = 0; d < D; ++d) {
+                if (adjoint)
+                  S += (int64_t)apar[d] * (kidx[(int64_t)dtile[o] * D + d] & 1);
+                else
+                  S += (int64_t)xidx[(int64_t)gtile[o] * D + d] * ((kidx[(int64_t)c0 * D + d] >> 1) & 1);
+              }
+              double ph = rho * (double)S;
+              ph -= std::floor(ph);
+              U.out_scale[v][0] = std::cos(2.0 * M_PI * ph);
+              U.out_scale[v][1] = (adjoint ? -1.0 : 1.0) * std::sin(2.0 * M_PI * ph);
+            }
+          }
       }
       // capacity: buffer 0 holds inputs (and pass 1 in 3D), buffer 1 pass 0
       const int need0 = std::max(tot_in + U.n_in, D == 3 ? tot[1] + U.n_pass[1] : 0);
       const int need1 = tot[0] + U.n_pass[0];
       const int needo = tot[D - 1] + U.n_pass[D - 1];
-      // header, two tasks and up to two groups per item, one run per output
-      const int needb = 64 + 32 * (need1 + (D == 3 ? tot[1] + U.n_pass[1] : 0) + needo) + 8 * needo + 15;
+      // header, an item and up to one group per item, one run and (rho != 1) one
+      // scalar per output, paddings
+      const int needb = kBlobHeader + 20 * (need1 + (D == 3 ? tot[1] + U.n_pass[1] : 0) + needo) + 8 * needo + 8 +
+                        15 + (scaled ? 16 * needo : 0);
       if (!units.empty() && (need0 > caps.cap0 || need1 > caps.cap1 || needo > caps.max_out ||
                              needb > caps.meta_bytes))
         flush();
@@ -377,7 +409,7 @@ StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp
   return prog;
 }
 
-std::string validate_program(const StageProgram &prog, int dim, ChunkCaps caps, int64_t in_tiles,
+std::string validate_program(const StageProgram &prog, int dim, int p, ChunkCaps caps, int64_t in_tiles,
                              int64_t out_tiles) {
   for (size_t ci = 0; ci < prog.chunks.size(); ++ci) {
     const ChunkDesc &c = prog.chunks[ci];
@@ -386,20 +418,22 @@ std::string validate_program(const StageProgram &prog, int dim, ChunkCaps caps, 
     if (c.n_in < 1 || c.n_in > caps.cap0 || n0 > caps.cap1 || n1 > caps.cap0 || nl > caps.max_out ||
         nl > stage_cap)
       return "chunk exceeds its shared-memory capacities";
-    if (c.blob_off < 0 || (c.blob_off & 15) || (size_t)c.blob_off + 64 > prog.blob.size())
+    if (c.blob_off < 0 || (c.blob_off & 15) || (size_t)c.blob_off + kBlobHeader > prog.blob.size())
       return "metadata blob out of range";
     const int32_t *hdr = reinterpret_cast<const int32_t *>(prog.blob.data() + c.blob_off);
-    int64_t ntasks = 0, ngroups = 0;
+    int64_t nitems = 0, ngroups = 0;
     for (int k = 0; k < dim; ++k) {
-      if (hdr[2 * k] != c.n_item[k] || hdr[2 * k + 1] < 0 || hdr[2 * k + 1] > hdr[2 * k])
+      if (hdr[k] != c.n_item[k] || hdr[3 + k] < (hdr[k] > 0) || hdr[3 + k] > hdr[k])
         return "metadata header mismatch";
-      ntasks += hdr[2 * k] + hdr[2 * k + 1];
-      ngroups += hdr[6 + 2 * k] + hdr[6 + 2 * k + 1];
+      nitems += hdr[k];
+      ngroups += hdr[3 + k];
     }
-    if (hdr[12] != c.n_in) return "metadata header mismatch";
-    const int n_oruns = hdr[13];
-    const int64_t need = (64 + ntasks * (int64_t)sizeof(Task) + ngroups * (int64_t)sizeof(Group) +
-                          n_oruns * (int64_t)sizeof(Run) + 15) & ~(int64_t)15;
+    if (hdr[6] != c.n_in || (hdr[8] != 0 && hdr[8] != 1) || hdr[9] || hdr[10] || hdr[11])
+      return "metadata header mismatch";
+    const int n_oruns = hdr[7];
+    const int64_t gpad = (ngroups * (int64_t)sizeof(Group) + 7) & ~(int64_t)7;
+    const int64_t soff = (kBlobHeader + nitems * (int64_t)sizeof(Item) + gpad + n_oruns * (int64_t)sizeof(Run) + 15) & ~(int64_t)15;
+    const int64_t need = soff + (hdr[8] ? (int64_t)c.n_item[dim - 1] * 16 : 0);
     if (c.blob_bytes != need || c.blob_bytes > caps.meta_bytes || (size_t)c.blob_off + c.blob_bytes > prog.blob.size())
       return "metadata blob out of range";
     if (c.run_off < 0 || c.n_runs < 1 || (size_t)c.run_off + c.n_runs > prog.runs.size())
@@ -412,9 +446,15 @@ std::string validate_program(const StageProgram &prog, int dim, ChunkCaps caps, 
       covered += rn.count;
     }
     if (covered != c.n_in) return "runs do not cover the inputs";
-    const Task *tasks = reinterpret_cast<const Task *>(prog.blob.data() + c.blob_off + 64);
-    const Group *groups = reinterpret_cast<const Group *>(tasks + ntasks);
-    const Run *oruns = reinterpret_cast<const Run *>(groups + ngroups);
+    const unsigned char *bp = prog.blob.data() + c.blob_off;
+    const Item *items = reinterpret_cast<const Item *>(bp + kBlobHeader);
+    const Group *groups = reinterpret_cast<const Group *>(bp + kBlobHeader + nitems * sizeof(Item));
+    const Run *oruns = reinterpret_cast<const Run *>(bp + kBlobHeader + nitems * sizeof(Item) + gpad);
+    if (hdr[8]) {
+      const double *sc = reinterpret_cast<const double *>(bp + soff);
+      for (int r = 0; r < c.n_item[dim - 1]; ++r)
+        if (!(std::fabs(std::hypot(sc[2 * r], sc[2 * r + 1]) - 1.0) < 1e-12)) return "output factor not of unit modulus";
+    }
     covered = 0;
     for (int r = 0; r < n_oruns; ++r) {
       const Run &rn = oruns[r];
@@ -423,32 +463,37 @@ std::string validate_program(const StageProgram &prog, int dim, ChunkCaps caps, 
       covered += rn.count;
     }
     if (covered != nl) return "output runs do not cover the outputs";
+    int fib = 1;
+    for (int d = 0; d + 1 < dim; ++d) fib *= p;
     int off = 0, goff = 0;
     int nsrc = c.n_in;  // sources of pass k live in the previous pass's buffer
     for (int k = 0; k < dim; ++k) {
-      for (int f = 0; f < 2; ++f) {
-        const int nt = hdr[2 * k + f], ng = hdr[6 + 2 * k + f];
-        std::vector<char> seen(c.n_item[k], 0);
-        for (int i = 0; i < nt; ++i) {
-          const Task &tk = tasks[off + i];
-          if (tk.src >= nsrc) return "task source out of range";
-          if (tk.dst >= c.n_item[k] || seen[tk.dst]) return "task destination out of range or repeated";
-          if (tk.op >= 64) return "task operator out of range";
-          seen[tk.dst] = 1;
-        }
-        int covered_t = 0;
-        for (int g = 0; g < ng; ++g) {
-          const Group &gr = groups[goff + g];
-          if (gr.task_begin != covered_t || gr.n_tasks < 1 || gr.task_begin + gr.n_tasks > nt)
-            return "operator groups do not tile the tasks";
-          for (int i = 0; i < gr.n_tasks; ++i)
-            if (tasks[off + gr.task_begin + i].op != gr.op) return "task outside its operator group";
-          covered_t += gr.n_tasks;
-        }
-        if (covered_t != nt) return "operator groups do not cover the tasks";
-        off += nt;
-        goff += ng;
+      const int ni = hdr[k], ng = hdr[3 + k];
+      std::vector<char> seen(c.n_item[k], 0);
+      for (int i = 0; i < ni; ++i) {
+        const Item &it = items[off + i];
+        if (it.src0 >= nsrc) return "item source 0 out of range";
+        if (it.src1 != 0xffff && it.src1 >= nsrc) return "item source 1 out of range";
+        if (it.dst >= c.n_item[k] || seen[it.dst]) return "item destination out of range or repeated";
+        seen[it.dst] = 1;
       }
+      int covered_i = 0, work = 0;
+      for (int g = 0; g < ng; ++g) {
+        const Group &gr = groups[goff + g];
+        if (gr.item_begin != covered_i || gr.n_items < 1 || gr.item_begin + gr.n_items > ni)
+          return "operator groups do not tile the items";
+        if (gr.work_begin != work) return "operator group work offsets inconsistent";
+        work += ((gr.n_items * fib + 31) / 32) * (gr.op1 == 0xffff ? 1 : 2);
+        if (work > 0xffff) return "pass work exceeds 16 bits";
+        if (gr.op0 >= 64 || (gr.op1 != 0xffff && gr.op1 >= 64)) return "operator out of range";
+        for (int i = 0; i < gr.n_items; ++i)
+          if ((items[off + gr.item_begin + i].src1 == 0xffff) != (gr.op1 == 0xffff))
+            return "item source count differs from its group";
+        covered_i += gr.n_items;
+      }
+      if (covered_i != ni) return "operator groups do not cover the items";
+      off += ni;
+      goff += ng;
       nsrc = c.n_item[k];
     }
   }

@@ -12,7 +12,7 @@
 struct bfly_plan_s {
   int dim = 0, p = 0, L = 0, prec = 1, max_nrhs = 1;
   unsigned flags = 0;
-  double N = 0;
+  double N = 0, rho = 1.0;  // leaves rho = N / 2^L wide
   int64_t nx = 0, nk = 0;
   int device = -1;
   bfly::HostTree TX, TK;
@@ -26,7 +26,7 @@ struct bfly_plan_s {
   char *dmem = nullptr;
   size_t dbytes = 0;
   int32_t *perm_x = nullptr, *perm_k = nullptr, *leaf_x = nullptr, *leaf_k = nullptr;
-  int32_t *pleaf_x = nullptr, *pleaf_k = nullptr, *lidx_x = nullptr;
+  int32_t *pleaf_x = nullptr, *pleaf_k = nullptr;
   double *off_x = nullptr, *off_k = nullptr, *xs = nullptr, *ks_ = nullptr, *inv_den = nullptr;
   void *Wx = nullptr, *Wk = nullptr, *table = nullptr, *tableH = nullptr;
   struct DevProg {

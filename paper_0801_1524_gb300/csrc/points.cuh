@@ -1,11 +1,13 @@
 // Steps 2 and 4 of Sec. 2.2 and their adjoints, and the per-point weights they use.
 //
 // Leaf step (step 2): for every leaf B of T_K the equivalent charges for the root A0 of
-// T_X are f^{A0 B} = sum_{j in B} f_j (x)_d w(tau_{j,d}), tau = k_j - b the offset of the
-// source in its unit leaf and w(tau) = G^{-1} v(tau) (eq. M1 with c^{A0} = 0).
-// Final step (step 4): u_i = sum_l prod_d rho_{l_d}(a_d, sigma_{i,d}) f^{A B0}_l with
-// rho_l(a, sigma) = exp(2 pi i ((a l mod q) + l sigma)/q), a the leaf index of x_i and
-// sigma = x_i - a (k^{B0}_l = l N/q).
+// T_X are f^{A0 B} = sum_{j in B} f_j (x)_d w(tau_{j,d}), tau = k_j / rho - b the offset of
+// the source in its leaf (rho = N / 2^L wide) and w(tau) = G^{-1} v(tau) (eq. M1 with
+// c^{A0} = 0).
+// Final step (step 4): u_i = sum_l prod_d e^{2 pi i rho l_d sigma_{i,d}/q} g^{A B0}_l, with
+// sigma = x_i / rho - a the offset of x_i in its leaf a (k^{B0}_l = l N/q) and g the
+// rescaled charges g_l = e^{2 pi i rho a l/q} f_l of the recursive step, which absorb
+// the leaf's own phase.
 // Both are "spread" (points -> one tile per leaf) or "interp" (one tile per leaf ->
 // points) with per-point weights W[point][d][l]; the adjoint sweep uses the other of
 // the two with conj(W).
@@ -88,26 +90,24 @@ __global__ void __launch_bounds__(256) interp_kernel(const PointArgs a) {
   store_io(a.vout, (int64_t)r * a.n_total + a.perm[i], acc, a.io64);
 }
 
-// Plan-time weights, computed in FP64 and stored in the plan's precision R.
+// Plan-time weights, computed in FP64 and stored in the plan's precision R; tau is the
+// offset of the point from its leaf corner in leaf widths, rho = N / 2^L the leaf width.
 //   kind 0 (T_K, step 2): W[j][d][m] = w_m(tau_{j,d}) by the Lagrange product form
-//          e^{i pi (tau - m/q)} prod_{n != m} sin(pi (tau - n/q)/q) * inv_den[m];
-//   kind 1 (T_X, step 4): W[i][d][l] = exp(2 pi i ((a_d l mod q) + l sigma_{i,d})/q).
+//          e^{i pi rho (tau - m/q)} prod_{n != m} sin(pi rho (tau - n/q)/q) * inv_den[m];
+//   kind 1 (T_X, step 4): W[i][d][l] = exp(2 pi i rho l tau_{i,d}/q).
 constexpr int kMaxP = 9;
 template <typename R>
-__global__ void weights_kernel(int64_t n, int dim, int p, int kind, const double *off,
-                               const int32_t *point_leaf, const int32_t *leaf_idx,
+__global__ void weights_kernel(int64_t n, int dim, int p, double rho, int kind, const double *off,
                                const double *inv_den, typename Cx<R>::T *W) {
   using C = typename Cx<R>::T;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * dim) return;
-  const int64_t i = t / dim;
-  const int d = (int)(t - i * dim);
   const int q = p - 1;
   const double tau = off[t];
   C *out = W + (size_t)t * p;
   if (kind == 0) {
     double s[kMaxP], pre[kMaxP + 1], suf[kMaxP + 1];
-    for (int n2 = 0; n2 < p; ++n2) s[n2] = sinpi((tau - (double)n2 / q) / q);
+    for (int n2 = 0; n2 < p; ++n2) s[n2] = sinpi(rho * (tau - (double)n2 / q) / q);
     pre[0] = 1.0;
     for (int n2 = 0; n2 < p; ++n2) pre[n2 + 1] = pre[n2] * s[n2];
     suf[p] = 1.0;
@@ -115,16 +115,13 @@ __global__ void weights_kernel(int64_t n, int dim, int p, int kind, const double
     for (int m = 0; m < p; ++m) {
       const double mag = pre[m] * suf[m + 1] * inv_den[m];
       double sn, cs;
-      sincospi(tau - (double)m / q, &sn, &cs);
+      sincospi(rho * (tau - (double)m / q), &sn, &cs);
       out[m] = cmk((R)(cs * mag), (R)(sn * mag));
     }
   } else {
-    const int a = leaf_idx[(size_t)point_leaf[i] * dim + d];
-    const int amod = a % q;
     for (int l = 0; l < p; ++l) {
-      const double ph = 2.0 * ((double)((amod * l) % q) + (double)l * tau) / q;
       double sn, cs;
-      sincospi(ph, &sn, &cs);
+      sincospi(2.0 * rho * (double)l * tau / q, &sn, &cs);
       out[l] = cmk((R)cs, (R)sn);
     }
   }

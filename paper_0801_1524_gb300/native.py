@@ -28,12 +28,14 @@ class Opts(ctypes.Structure):
 
 class PlanInfo(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("p", ctypes.c_int), ("L", ctypes.c_int),
-                ("prec", ctypes.c_int), ("N", ctypes.c_double), ("nx", ctypes.c_int64),
+                ("prec", ctypes.c_int), ("N", ctypes.c_double), ("rho", ctypes.c_double),
+                ("nx", ctypes.c_int64),
                 ("nk", ctypes.c_int64), ("total_pairs", ctypes.c_int64),
                 ("max_pairs", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
                 ("tiles_read_fwd", ctypes.c_int64), ("tiles_written_fwd", ctypes.c_int64),
                 ("jobs_fwd", ctypes.c_int64), ("chunks_fwd", ctypes.c_int64),
-                ("flops_fwd", ctypes.c_double), ("smem_kb", ctypes.c_int),
+                ("flops_fwd", ctypes.c_double), ("lane_use_fwd", ctypes.c_double),
+                ("smem_kb", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("tuned_ms", ctypes.c_double),
                 ("plan_seconds", ctypes.c_double)]
 

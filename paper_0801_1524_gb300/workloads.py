@@ -105,13 +105,15 @@ def gaussian_sources(n: int, nrhs: int = 1, seed: int = 0, dtype=np.complex128):
 
 
 def random_points(n: int, N: float, dim: int, seed: int, edge_fraction: float = 0.0):
-    """Uniform points in [0,N]^dim; a fraction is snapped to box edges and to N itself."""
+    """Uniform points in [0,N]^dim; a fraction is snapped to the dyadic grid of spacing
+    h = N / 2^ceil(log2 N) (the unit grid when N is a power of two) and to N itself."""
     rng = np.random.default_rng(seed)
     pts = rng.uniform(0.0, float(N), size=(n, dim))
     if edge_fraction > 0 and n > 0:
         m = max(1, int(edge_fraction * n))
         idx = rng.choice(n, size=min(m, n), replace=False)
-        pts[idx] = np.floor(pts[idx])
+        h = float(N) / 2.0 ** max(0, math.ceil(math.log2(float(N)) - 1e-12)) if N > 1 else float(N)
+        pts[idx] = np.floor(pts[idx] / h) * h
         if len(idx) > 1:
             pts[idx[0], :] = float(N)
             pts[idx[1], 0] = float(N)
@@ -168,16 +170,18 @@ def star32768(p: int = 7) -> Instance:
 
 
 def batch_sizes(count: int = 64, lo: float = 512.0, hi: float = 16384.0, seed: int = 0):
-    """N_i log-uniform in [lo, hi] from default_rng(seed); also the nearest powers of two."""
+    """N_i log-uniform in [lo, hi] from default_rng(seed) (real-valued, as drawn), and the
+    nearest powers of two (a comparison setting with unit leaves only)."""
     rng = np.random.default_rng(seed)
     n_exact = np.exp(rng.uniform(math.log(lo), math.log(hi), size=count))
     n_pow2 = 2.0 ** np.round(np.log2(n_exact))
     return n_exact, n_pow2
 
 
-def star_batch(count: int = 64, p: int = 7, nrhs: int = 16, power_of_two: bool = True,
+def star_batch(count: int = 64, p: int = 7, nrhs: int = 16, power_of_two: bool = False,
                seed: int = 0) -> list[Instance]:
-    """64 instances of star-shaped curve pairs; instance i uses X seed 2i+1000, K seed 2i+1001."""
+    """64 instances of star-shaped curve pairs of the drawn N (power_of_two: rounded to the
+    nearest power of two); instance i uses X seed 2i+1000, K seed 2i+1001."""
     n_exact, n_pow2 = batch_sizes(count, seed=seed)
     out = []
     for i in range(count):

@@ -52,7 +52,7 @@ def _create(dim=2, N=16.0, x=None, k=None, p=5, flags=native.BFLY_FLAG_HOST_ONLY
 
 @pytest.mark.parametrize("kw,status", [
     (dict(dim=4), 1), (dict(dim=1), 1), (dict(p=2), 1), (dict(p=11), 1), (dict(p=4), 4),
-    (dict(N=24.0), 4), (dict(N=0.0), 1), (dict(N=float("nan")), 1),
+    (dict(N=-3.0), 1), (dict(N=0.0), 1), (dict(N=float("nan")), 1), (dict(N=float("inf")), 1),
     (dict(x=np.array([[1.0, 17.0]])), 1), (dict(k=np.array([[-0.5, 1.0]])), 1),
     (dict(k=np.array([[np.nan, 1.0]])), 1), (dict(prec=7), 1),
 ])
@@ -72,6 +72,8 @@ def test_null_and_host_only_execution_rejected():
 
 @pytest.mark.parametrize("dim,N,p,nx,nk,seed", [
     (2, 1.0, 5, 7, 9, 1), (2, 64.0, 5, 300, 200, 2), (3, 16.0, 3, 400, 300, 3), (2, 2.0, 7, 20, 20, 4),
+    # N not a power of two: leaves N / 2^L wide
+    (2, 24.0, 5, 300, 200, 5), (3, 12.0, 3, 300, 300, 6), (2, 0.75, 5, 10, 10, 7), (2, 1000.5, 7, 400, 400, 8),
 ])
 def test_stage_sizes_match_oracle_trees(dim, N, p, nx, nk, seed):
     inst = w.small_random(dim, N, p, nx, nk, seed, edge_fraction=0.3)
@@ -81,7 +83,9 @@ def test_stage_sizes_match_oracle_trees(dim, N, p, nx, nk, seed):
     assert got == ref
     info = P.info()
     assert info["total_pairs"] == sum(a * b for a, b in ref.values())
-    assert info["L"] == int(np.log2(N))
+    assert info["L"] == ob.levels_for(N)
+    assert info["rho"] == N / 2.0 ** info["L"]
+    assert 0.5 < info["rho"] <= 1.0 or N <= 1.0
 
 
 def test_curve_workload_plan_counts():

@@ -22,7 +22,8 @@ def _gpu(a, dtype=torch.complex128):
     return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
 
 
-@pytest.mark.parametrize("dim,N,p", [(2, 64.0, 5), (2, 256.0, 7), (3, 8.0, 5), (2, 1.0, 3)])
+@pytest.mark.parametrize("dim,N,p", [(2, 64.0, 5), (2, 256.0, 7), (3, 8.0, 5), (2, 1.0, 3), (2, 300.0, 7),
+                                     (3, 10.0, 5)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_dot_product_identity(dim, N, p, prec):
     inst = w.small_random(dim, N, p, 700, 600, 21)
@@ -35,7 +36,7 @@ def test_dot_product_identity(dim, N, p, prec):
     assert abs(lhs - rhs) / scale < (1e-13 if prec == "fp64" else 1e-6)
 
 
-@pytest.mark.parametrize("dim,N,p", [(2, 16.0, 5), (3, 4.0, 3)])
+@pytest.mark.parametrize("dim,N,p", [(2, 16.0, 5), (3, 4.0, 3), (2, 20.0, 5), (3, 6.0, 3)])
 def test_adjoint_equals_transpose_of_oracle_matrix(dim, N, p):
     inst = w.small_random(dim, N, p, 60, 50, 23)
     B = ob.butterfly_matrix(inst.x, inst.k, N, p)       # [nx, nk] from the oracle

@@ -13,19 +13,23 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def _instances():
+def _instances(sizes=(64.0, 512.0, 128.0, 1024.0, 32.0, 256.0)):
     out = []
-    for i, N in enumerate([64.0, 512.0, 128.0, 1024.0, 32.0, 256.0]):
+    for i, N in enumerate(sizes):
         x = w.sample_curve(w.star_curve(2 * i + 1000), N)
         k = w.sample_curve(w.star_curve(2 * i + 1001), N)
         out.append(w.Instance(f"b{i}", 2, N, 7, x, k, nrhs=3, f_seed=i))
     return out
 
 
+GENERAL_N = (64.0, 700.5, 128.0, 1000.0, 40.0, 300.25)  # powers of two and not
+
+
+@pytest.mark.parametrize("sizes", ["pow2", "general"])
 @pytest.mark.parametrize("prec,dtype", [("fp32", torch.complex64), ("fp64", torch.complex128)])
-def test_batch_matches_plans_and_oracle(prec, dtype):
+def test_batch_matches_plans_and_oracle(prec, dtype, sizes):
     from paper_0801_1524_gb300.plan import Batch, Plan
-    insts = _instances()
+    insts = _instances() if sizes == "pow2" else _instances(GENERAL_N)
     plans = [Plan(I.x, I.k, I.N, I.p, precision=prec, max_nrhs=3) for I in insts]
     batch = Batch(plans)
     fs = [torch.as_tensor(I.sources(), dtype=dtype, device="cuda") for I in insts]

@@ -53,6 +53,12 @@ SMALL = [
     (3, 4.0, 3, 200, 150, 6),
     (3, 8.0, 5, 400, 300, 7),
     (3, 4.0, 7, 150, 120, 8),
+    # N not a power of two: leaves N / 2^L wide, a unit-modulus factor per output tile
+    (2, 24.0, 5, 300, 250, 9),
+    (2, 0.75, 5, 30, 25, 10),
+    (2, 100.5, 7, 600, 500, 11),
+    (3, 12.0, 5, 400, 300, 12),
+    (3, 6.0, 3, 200, 200, 13),
 ]
 
 
@@ -66,7 +72,7 @@ def test_random_points_match_oracle(dim, N, p, nx, nk, seed, prec):
     assert rel_l2(got, ref) < (TOL64 if prec == "fp64" else tol32(p))
 
 
-@pytest.mark.parametrize("N,p", [(256.0, 5), (256.0, 7), (1024.0, 7), (512.0, 9)])
+@pytest.mark.parametrize("N,p", [(256.0, 5), (256.0, 7), (1024.0, 7), (512.0, 9), (700.0, 7), (1500.3, 5)])
 def test_curves_match_oracle_and_band(N, p):
     x = w.sample_curve(w.circle_curve(), N)
     k = w.sample_curve(w.perturbed_ellipse_curve(), N)
