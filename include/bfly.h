@@ -74,7 +74,7 @@ typedef struct {
   int dim, p, L;                /* L = ceil(log2 N) levels below the root (0 if N <= 1) */
   int prec;                     /* bfly_precision of the plan */
   double N;
-  double rho;                   /* leaf width N / 2^L, in (1/2, 1]; 1 when N = 2^L */
+  double rho;                   /* N / 2^L, in (1/2, 1]; the points are scaled by 1/sqrt(rho) */
   int64_t nx, nk;               /* number of targets and sources */
   int64_t total_pairs;          /* sum over stages t of nA(L-t) * nK(t) */
   int64_t max_pairs;            /* largest stage */
@@ -93,16 +93,16 @@ typedef struct {
 } bfly_plan_info_t;
 
 /*
- * bfly_plan_create — Sec. 2.2 step 1 and everything that depends only on the points:
- * scales nothing (the points are already in [0,N]^dim), builds L = ceil(log2 N) levels
- * below the root with leaves of width rho = N / 2^L (unit leaves when N is a power of
- * two, the setting of Sec. 2.2; otherwise w^A w^B = rho N <= N, which keeps the rank
- * bound of Theorem 2.1), assigns every point to its leaf (index min(floor(x / rho),
- * 2^L - 1) per axis), sorts the points by leaf in Morton order, builds the non-empty
- * boxes of every level of T_X and T_K with their child ranges, the transfer operators
- * (eqs. M1 and E1 combined, built in FP64), and the per-point interpolation weights of
- * steps 2 and 4; uploads all of it and allocates two charge buffers of the largest stage
- * (Sec. 2.2: two adjacent levels are live).
+ * bfly_plan_create — Sec. 2.2 step 1 and everything that depends only on the points.
+ * With L = ceil(log2 N) and s = sqrt(2^L / N) (s = 1 when N is a power of two, the
+ * setting of Sec. 2.2), x.k/N = (s x).(s k)/2^L: the plan builds the transform of
+ * N' = 2^L on the scaled points, which lie in [0, 2^L]^dim, with unit leaves.  It assigns
+ * every scaled point to its leaf (index min(floor(s x), 2^L - 1) per axis), sorts the
+ * points by leaf in Morton order, builds the non-empty boxes of every level of T_X and
+ * T_K with their child ranges, the transfer operators (eqs. M1 and E1 combined, built in
+ * FP64), and the per-point interpolation weights of steps 2 and 4; uploads all of it and
+ * allocates two charge buffers of the largest stage (Sec. 2.2: two adjacent levels are
+ * live).
  *   out      receives the plan; *out is NULL on failure.
  *   dim      2 or 3.   N: finite, > 0.   p: 3, 5, 7 or 9.
  *   x, k     host arrays [nx][dim] and [nk][dim], every coordinate finite and in [0,N];
@@ -212,7 +212,7 @@ bfly_status bfly_device_status(bfly_plan_t plan, int *flags);
  *
  * bfly_batch_create — plans: count device plans (the caller keeps ownership and must
  *   keep them alive while the batch exists).  The plans must have been created with the
- *   same shared-memory budget (smem_kb); each keeps its own operators (its own N).
+ *   same shared-memory budget (smem_kb).
  *   Errors: INVALID_ARG (NULL, host-only plans, mixed dim / p / precision / device /
  *   tile capacities), UNSUPPORTED, OUT_OF_MEMORY, CUDA.
  * bfly_batch_execute — f[i] (device, [nrhs][nk_i]) -> u[i] (device, [nrhs][nx_i]) for

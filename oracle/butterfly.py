@@ -5,8 +5,7 @@ The butterfly algorithm of Sec. 2.2 written out step by step in float64 numpy, i
 paper's notation, with nothing precomputed or fused:
 
   Step 1  build T_X and T_K: boxes of width w_s = N / 2^s at levels s = 0..L, leaves
-          of unit width when N = 2^L (for other N: L = ceil(log2 N), leaf width N/2^L),
-          non-empty boxes only (Sec. 2.2 operation count).
+          of unit width (N = 2^L), non-empty boxes only (Sec. 2.2 operation count).
   Step 2  for each leaf B of T_K, the check potentials u^{A0 B} at the grid x^{A0}_l of
           the root A0 of T_X by direct summation over the sources in B, then the
           equivalent charges f^{A0 B} on the grid k^B_l from M f = u (Sec. 2.1).
@@ -27,7 +26,11 @@ diagonal x H x diagonal (eqs. M1 and E1) is deliberately not used here.
 Readings where the paper is silent: a point on a box edge belongs to the box with the
 larger index, except at the far edge N (index clamped to 2^s - 1); boxes of a level are
 the non-empty ones; a missing child of B contributes nothing; the matching systems are
-solved by LU with partial pivoting (numpy.linalg.solve).
+solved by LU with partial pivoting (numpy.linalg.solve).  N not a power of two (the
+paper's setting has unit leaves, N = 2^L): with L = ceil(log2 N) and rho = N / 2^L,
+x.k/N = x'.k'/2^L for x' = x s, k' = k s, s = sqrt(2^L / N), so the transform is the one
+of N' = 2^L on the scaled points, which lie in [0, 2^L sqrt(rho)]^d; the butterfly is
+run on those (unit leaves, w^A w^B = N').
 """
 from __future__ import annotations
 
@@ -44,10 +47,21 @@ def cis(phi):
 
 
 def levels_for(N: float) -> int:
-    """L with leaf width N / 2^L = 1 for N = 2^L; L = ceil(log2 N) otherwise (0 for N <= 1)."""
+    """L = log2 N for N = 2^L; L = ceil(log2 N) otherwise (0 for N <= 1)."""
     if N <= 1.0:
         return 0
     return int(math.ceil(math.log2(N) - 1e-12))
+
+
+def power_of_two_form(x, k, N):
+    """(x', k', N') with N' = 2^L and x'.k'/N' = x.k/N: the points scaled by sqrt(N'/N)
+    (unchanged when N is a power of two)."""
+    L = levels_for(float(N))
+    Np = 2.0 ** L
+    if Np == float(N):
+        return x, k, Np
+    s = math.sqrt(Np / float(N))
+    return x * s, k * s, Np
 
 
 class Tree:
@@ -211,7 +225,7 @@ def butterfly(x, k, f, N, p, dense: bool = False, stats: list | None = None):
     k = np.asarray(k, dtype=np.float64)
     if p < 3:
         raise ValueError("p >= 3: for p = 2 the matching matrix is singular")
-    N = float(N)
+    x, k, N = power_of_two_form(x, k, float(N))
     L = levels_for(N)
     TX = Tree(x, N, L)
     TK = Tree(k, N, L)
@@ -231,6 +245,7 @@ def butterfly_matrix(x, k, N, p, dense: bool = False):
 
 def pair_counts(x, k, N):
     """Stage t -> (non-empty T_X boxes at level L-t) x (non-empty T_K boxes at level t)."""
-    L = levels_for(float(N))
-    TX, TK = Tree(np.asarray(x, float), N, L), Tree(np.asarray(k, float), N, L)
+    x, k, N = power_of_two_form(np.asarray(x, float), np.asarray(k, float), float(N))
+    L = levels_for(N)
+    TX, TK = Tree(x, N, L), Tree(k, N, L)
     return {t: (TX.boxes[L - t].shape[0], TK.boxes[t].shape[0]) for t in range(L + 1)}

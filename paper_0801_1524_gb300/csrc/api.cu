@@ -75,7 +75,8 @@ struct Arena {
 };
 
 // Levels below the root: the smallest L with 2^L >= N (up to a relative 1e-12), 0 for
-// N <= 1; the leaves are rho = N / 2^L wide, rho = 1 exactly when N = 2^L.
+// N <= 1.  The points are scaled by sqrt(2^L / N) so that the transform is the one of
+// N' = 2^L (x.k/N = x'.k'/N').
 int levels_for(double N) {
   if (!(N > 1.0)) return 0;
   return (int)std::ceil(std::log2(N) - 1e-12);
@@ -145,13 +146,14 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   P->L = L;
   P->N = N;
   P->rho = std::ldexp(N, -L);  // exact
+  P->scale = P->rho == 1.0 ? 1.0 : std::sqrt(std::ldexp(1.0, L) / N);
   P->nx = nx;
   P->nk = nk;
   P->prec = o.prec;
   P->max_nrhs = o.max_nrhs;
   P->flags = o.flags;
-  std::string err = bfly::build_tree(P->TX, dim, L, P->rho, nx, x);
-  if (err.empty()) err = bfly::build_tree(P->TK, dim, L, P->rho, nk, k);
+  std::string err = bfly::build_tree(P->TX, dim, L, N, P->scale, nx, x);
+  if (err.empty()) err = bfly::build_tree(P->TK, dim, L, N, P->scale, nk, k);
   if (!err.empty()) {
     delete P;
     return fail(BFLY_ERR_INVALID_ARG, err);
@@ -207,22 +209,15 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   P->TS = P->ks->tile_stride;
   // capacities: the largest chunk that fits the shared-memory budget of one block
   const size_t want = (size_t)(o.smem_kb > 0 ? o.smem_kb : 55) * 1024;
-  // The tile capacities follow from the budget alone (so that plans of any N made with
-  // one budget can share a batched launch); a plan with N != 2^L then adds its output
-  // factors to the metadata slots, a little above the budget.
-  const bool scaled = P->rho != 1.0;
-  auto caps_for = [&](size_t budget, bool count_scalars) {
+  auto caps_for = [&](size_t budget) {
     for (int cap = 1024; cap >= 8; cap -= 8) {
-      ChunkCaps c{cap, cap, cap, P->ks->meta_bytes(cap, cap, cap, count_scalars)};
-      if (P->ks->level_smem(c) <= budget) {
-        c.meta_bytes = P->ks->meta_bytes(cap, cap, cap, scaled);
-        if (P->ks->level_smem(c) <= max_smem) return c;
-      }
+      const ChunkCaps c{cap, cap, cap, P->ks->meta_bytes(cap, cap, cap)};
+      if (P->ks->level_smem(c) <= budget) return c;
     }
     return ChunkCaps{0, 0, 0, 0};
   };
-  ChunkCaps caps = caps_for(std::min(want, max_smem), false);
-  if (caps.cap0 == 0) caps = caps_for(max_smem, true);
+  ChunkCaps caps = caps_for(std::min(want, max_smem));
+  if (caps.cap0 == 0) caps = caps_for(max_smem);
   if (caps.cap0 == 0) {
     delete P;
     return fail(BFLY_ERR_UNSUPPORTED, "charge tiles of this (dim, p, precision) do not fit in shared memory");
@@ -235,8 +230,8 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   for (int t = 0; t < L; ++t) {
     const auto &csAp = P->TX.cs[L - t - 1], &xidx = P->TX.idx[L - t];
     const auto &csB = P->TK.cs[t], &kidx = P->TK.idx[t + 1];
-    P->progF[t] = bfly::make_stage_program(dim, p, P->rho, csAp, xidx, csB, kidx, false, caps);
-    P->progA[t] = bfly::make_stage_program(dim, p, P->rho, csAp, xidx, csB, kidx, true, caps);
+    P->progF[t] = bfly::make_stage_program(dim, p, csAp, xidx, csB, kidx, false, caps);
+    P->progA[t] = bfly::make_stage_program(dim, p, csAp, xidx, csB, kidx, true, caps);
     for (int dir = 0; dir < 2; ++dir) {
       const int64_t tin = dir ? P->pairs[t] : P->pairs[t + 1], tout = dir ? P->pairs[t + 1] : P->pairs[t];
       const std::string bad = bfly::validate_program(dir ? P->progA[t] : P->progF[t], dim, p, caps, tin, tout);
@@ -255,14 +250,11 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
       for (int k = 0; k < dim; ++k) ni += hdr[k];
       const bfly::Item *it = reinterpret_cast<const bfly::Item *>(bp + bfly::kBlobHeader);
       for (int64_t i = 0; i < ni; ++i) srcs += 1 + (it[i].src1 != 0xffff);
-      // lanes used by the steps of every operator group (32 fibres per step)
-      const bfly::Group *gr = reinterpret_cast<const bfly::Group *>(it + ni);
-      int64_t ng = 0;
-      for (int k = 0; k < dim; ++k) ng += hdr[3 + k];
-      for (int64_t g = 0; g < ng; ++g) {
-        const int64_t fibres = (int64_t)gr[g].n_items * (PD / p), w = gr[g].op1 == 0xffff ? 1 : 2;
-        lanes_used += fibres * w;
-        lanes_issued += (fibres + 31) / 32 * 32 * w;
+      // lanes used by the steps of every pass (32 fibres per step, two-source fibres first)
+      for (int k = 0; k < dim; ++k) {
+        const int64_t nf = (int64_t)hdr[k] * (PD / p), nf2 = (int64_t)hdr[3 + k] * (PD / p);
+        lanes_used += nf + nf2;
+        lanes_issued += ((nf + 31) / 32 + (nf2 + 31) / 32) * 32;
       }
     }
     double fib_p2 = 1.0;  // fibres x p^2 complex multiply-adds per source, 8 flops each
@@ -283,10 +275,10 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   for (int m = 0; m < p; ++m) {
     double den = 1.0;
     for (int n2 = 0; n2 < p; ++n2)
-      if (n2 != m) den *= std::sin(M_PI * P->rho * ((double)(m - n2) / ((double)q * q)));
+      if (n2 != m) den *= std::sin(M_PI * ((double)(m - n2) / ((double)q * q)));
     inv_den[m] = 1.0 / den;
   }
-  std::vector<double> tabF = bfly::transfer_table(p, P->rho, false), tabH = bfly::transfer_table(p, P->rho, true);
+  std::vector<double> tabF = bfly::transfer_table(p, false), tabH = bfly::transfer_table(p, true);
   // FP32 operators for the recursive step: [op][l][m], m padded to an even count
   std::vector<float> tabF32, tabH32;
   if (o.prec == BFLY_PREC_FP32) {
@@ -363,11 +355,9 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     at += (it.bytes + 255) & ~(size_t)255;
   }
   if (e == cudaSuccess)
-    e = bfly::launch_weights(o.prec == BFLY_PREC_FP64 ? 0 : 1, nk, dim, p, P->rho, 0, P->off_k, P->inv_den,
-                             P->Wk, 0);
+    e = bfly::launch_weights(o.prec == BFLY_PREC_FP64 ? 0 : 1, nk, dim, p, 0, P->off_k, P->inv_den, P->Wk, 0);
   if (e == cudaSuccess)
-    e = bfly::launch_weights(o.prec == BFLY_PREC_FP64 ? 0 : 1, nx, dim, p, P->rho, 1, P->off_x, P->inv_den,
-                             P->Wx, 0);
+    e = bfly::launch_weights(o.prec == BFLY_PREC_FP64 ? 0 : 1, nx, dim, p, 1, P->off_x, P->inv_den, P->Wx, 0);
   int blocks = 0;
   if (e == cudaSuccess) e = P->ks->level_setup(P->level_smem, &blocks);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

@@ -1,6 +1,6 @@
 // Batched execution of many plans (independent transforms of uneven N and point counts,
 // each with nrhs right-hand sides; the plans share dim, p, precision and tile capacities,
-// each keeps its own operators): the leaf step of every plan, then one launch of the
+// and so the operators): the leaf step of every plan, then one launch of the
 // recursive-step kernel per stage t = L_max-1 .. 0 over the chunks of every plan that
 // has that stage (plans are aligned at the final stage), then the final step of every
 // plan.  On a non-default stream the whole sequence is captured once into a CUDA graph
@@ -53,7 +53,7 @@ bfly_status launch_all(bfly_batch_t B, const void *const *f, void *const *u, int
   bfly_plan_t P0 = B->plans[0];
   for (int t = B->L_max - 1; t >= 0; --t) {
     if (B->n_entries[t] == 0) continue;
-    // the tile capacities of plan 0 serve all; every entry names its plan's operators
+    // the operators and tile capacities of plan 0 serve all (same dim, p, precision)
     bfly::LevelArgs a{};
     a.nrhs = nrhs;
     a.entries = B->entries[t];
@@ -140,8 +140,6 @@ bfly_status bfly_batch_create(bfly_batch_t *out, int count, const bfly_plan_t *p
         e.out = P->buf[t & 1];
         e.in_rhs = P->pairs[t + 1] * P->TS;
         e.out_rhs = P->pairs[t] * P->TS;
-        e.table = P->table;
-        e.pad = 0;
         host[t].push_back(e);
       }
     }

@@ -48,6 +48,19 @@ __device__ __forceinline__ C cconj(C a) {
   a.y = -a.y;
   return a;
 }
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) {
+  a.x += b.x;
+  a.y += b.y;
+  return a;
+}
+// The value of lane (lane ^ mask) of the warp (all lanes take part).
+template <typename C>
+__device__ __forceinline__ C shfl_xor_c(C a, int mask) {
+  a.x = __shfl_xor_sync(0xffffffffu, a.x, mask);
+  a.y = __shfl_xor_sync(0xffffffffu, a.y, mask);
+  return a;
+}
 
 // Loads element i of an interleaved complex array of float or double as C.
 template <typename C>
@@ -88,7 +101,7 @@ struct LevelArgs {
   int nchunks;
   const unsigned char *blob;    // per-chunk metadata blobs (plan.hpp)
   const Run *runs;
-  const void *table;            // [4q][P][P] complex operators (conjugate-transposed: adjoint)
+  const void *table;            // [4][P][P] complex operators (conjugate-transposed: adjoint)
   int cap0, cap1, meta_bytes;   // shared-memory capacities the program was compiled for
   long long wait_limit;         // clock cycles before a wait gives up
   int *status;                  // device status word: bits set on a timeout

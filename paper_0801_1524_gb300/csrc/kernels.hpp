@@ -14,7 +14,7 @@ struct KernelSet {
   // per SM resident with `smem` bytes each
   cudaError_t (*level_setup)(size_t smem, int *blocks_per_sm);
   size_t (*level_smem)(const ChunkCaps &caps);
-  int (*meta_bytes)(int cap0, int cap1, int max_out, bool scaled);
+  int (*meta_bytes)(int cap0, int cap1, int max_out);
   size_t level_table_bytes, level_tile_bytes;
   int tile_stride;  // complex elements per stored charge tile
   cudaError_t (*spread)(const PointArgs &a, cudaStream_t s);
@@ -28,7 +28,7 @@ const KernelSet *kernels_p5(int prec, int dim);
 const KernelSet *kernels_p7(int prec, int dim);
 const KernelSet *kernels_p9(int prec, int dim);
 
-cudaError_t launch_weights(int prec, int64_t n, int dim, int p, double rho, int kind, const double *off,
+cudaError_t launch_weights(int prec, int64_t n, int dim, int p, int kind, const double *off,
                            const double *inv_den, void *W, cudaStream_t s);
 cudaError_t launch_direct(int prec, int dim, double N, int64_t nt, const double *xt, int64_t ns,
                           const double *xs, const void *in, void *out, int nrhs, bool io64,

@@ -30,21 +30,20 @@ struct Impl {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, level_kernel<R, D, P>, kLevelThreads, smem);
   }
   static size_t level_smem(const ChunkCaps &c) { return S::bytes(c); }
-  static int meta_bytes(int cap0, int cap1, int max_out, bool scaled) {
-    return S::meta_bytes(cap0, cap1, max_out, scaled);
-  }
+  static int meta_bytes(int cap0, int cap1, int max_out) { return S::meta_bytes(cap0, cap1, max_out); }
   static cudaError_t spread(const PointArgs &a, cudaStream_t s) {
     constexpr int PD = ipow(P, D);
     const int64_t work = a.nbox * PD;
     if (work == 0) return cudaSuccess;
-    dim3 grid((unsigned)((work + 255) / 256), (unsigned)a.nrhs);
-    spread_kernel<R, D, P><<<grid, 256, 0, s>>>(a);
+    dim3 grid((unsigned)((work + kPointThreads - 1) / kPointThreads), (unsigned)a.nrhs);
+    spread_kernel<R, D, P><<<grid, kPointThreads, 0, s>>>(a);
     return cudaGetLastError();
   }
   static cudaError_t interp(const PointArgs &a, cudaStream_t s) {
     if (a.n_total == 0) return cudaSuccess;
-    dim3 grid((unsigned)((a.n_total + 255) / 256), (unsigned)a.nrhs);
-    interp_kernel<R, D, P><<<grid, 256, 0, s>>>(a);
+    const int64_t lanes = a.n_total * kInterpLanes;
+    dim3 grid((unsigned)((lanes + kPointThreads - 1) / kPointThreads), (unsigned)a.nrhs);
+    interp_kernel<R, D, P><<<grid, kPointThreads, 0, s>>>(a);
     return cudaGetLastError();
   }
   static const KernelSet *get() {

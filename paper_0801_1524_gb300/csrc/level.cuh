@@ -17,13 +17,12 @@
 // output runs, cp.async.bulk shared -> global), waits until those stores have read the
 // slot, then copies chunk i's metadata blob and input tiles (runs of consecutive 16-byte
 // aligned tiles) into the slot with bulk copies completing on the slot's "full" mbarrier.
-// The consumer warps wait on "full" and run the passes.  A pass's items are grouped by
-// their pair of operators (op0 for the first source, op1 for the second, if any); a
-// group's fibres are taken 32 at a time ("steps", one fibre per lane), the warps split
-// the pass's work (one unit per source of a step) evenly, and every lane of a step
-// computes y = T^{op0} x0 (+ T^{op1} x1) for its fibre with operator reads that are
-// broadcasts (the same operators in every lane, so no divergence): P or 2P loads, P^2 or
-// 2P^2 complex multiply-adds and P stores per fibre, one barrier per pass.  The last
+// The consumer warps wait on "full" and run the passes.  A pass's fibres (two-source
+// items first) are taken 32 at a time ("steps", one fibre per lane), the warps split the
+// pass's work (one unit per source of a step) evenly, and every lane of a step computes
+// y = C^{op0} x0 (+ C^{op1} x1) for its fibre with its item's operators (four operators,
+// laid out so that any mix of them in a warp reads in one wavefront): P or 2P loads, P^2
+// or 2P^2 complex multiply-adds and P stores per fibre, one barrier per pass.  The last
 // pass stages its tiles in the slot; the consumers then signal
 // the slot's "staged" mbarrier and go on with the other slot, so that the write-back and
 // the next copies overlap their compute.  Every mbarrier wait gives up after a clock
@@ -57,19 +56,25 @@ struct LevelShape {
   // one 16-byte load reads T[m][l] and T[m+1][l]; FP64 operators as [op][m][l]
   static constexpr int PP = sizeof(R) == 4 ? (P + 1) & ~1 : P;
   static constexpr int OPS = sizeof(R) == 4 ? P * PP : P * P;  // elements per operator
-  static constexpr size_t table_bytes = (size_t)NOPS * OPS * sizeof(C);
+  // In shared memory the operators are OPS_S elements apart, a stride of 8 (mod 32)
+  // words: the same entry of the four operators then lies in four different groups of
+  // banks, so that a warp whose lanes use different operators still reads them in one
+  // wavefront.
+  static constexpr int OPW = OPS * (int)(sizeof(C) / 4);  // words per operator
+  static constexpr int OPS_S = (OPW + ((8 - OPW % 32) + 32) % 32) / (int)(sizeof(C) / 4);
+  static constexpr size_t table_bytes = (size_t)NOPS * OPS * sizeof(C);  // global layout
+  static constexpr size_t smem_table_bytes = (size_t)NOPS * OPS_S * sizeof(C);
   static constexpr size_t tile_bytes = (size_t)TS * sizeof(C);
-  static int meta_bytes(int cap0, int cap1, int max_out, bool scaled) {
-    // header, an item (8 bytes) and at most one operator group (12 bytes) per item, one
-    // run (8 bytes) and, for scaled programs, one FP64 complex factor per output, paddings
+  static int meta_bytes(int cap0, int cap1, int max_out) {
+    // header, an item (8 bytes) per pass tile, one run (8 bytes) per output, padding
     const int items = cap1 + (D == 3 ? cap0 : 0) + max_out;
-    return (kBlobHeader + 20 * items + 8 * max_out + 8 + 15 + (scaled ? 16 * max_out : 0)) & ~15;
+    return (kBlobHeader + 8 * items + 8 * max_out + 15) & ~15;
   }
   // table | 4 mbarriers | 2 metadata slots | 2 input buffers | scratch (2 in 3D, where
   // the last pass stages its outputs there)
   static constexpr int NSCR = D == 3 ? 2 : 1;
   static size_t bytes(const ChunkCaps &c) {
-    size_t b = (table_bytes + 15) & ~(size_t)15;
+    size_t b = (smem_table_bytes + 15) & ~(size_t)15;
     b += 64;
     b += 2 * (size_t)c.meta_bytes;
     return b + (2 * (size_t)c.cap0 + NSCR * (size_t)c.cap1) * tile_bytes;
@@ -149,7 +154,7 @@ __device__ __forceinline__ bool consumer_any(bool v) {
 }
 
 // Accumulates y += T x for one fibre: x[l] = X[l * SK], T the operator at Tg (FP32:
-// transposed and padded, one 16-byte broadcast read gives T[m][l] and T[m+1][l]).
+// transposed and padded, one 16-byte read gives T[m][l] and T[m+1][l]).
 template <typename R, int P, int PP, int SK>
 __device__ __forceinline__ void apply_op(const typename Cx<R>::T *Tg, const typename Cx<R>::T *X,
                                          typename Cx<R>::T (&y)[P]) {
@@ -160,7 +165,7 @@ __device__ __forceinline__ void apply_op(const typename Cx<R>::T *Tg, const type
   // l outer, m inner: P independent multiply-add chains in flight
 #pragma unroll
   for (int l = 0; l < P; ++l) {
-    if (sizeof(R) == 4) {
+    if constexpr (sizeof(R) == 4) {
       const float4 *Tl = reinterpret_cast<const float4 *>(Tg + l * PP);
 #pragma unroll
       for (int m = 0; m < P; m += 2) {
@@ -175,60 +180,44 @@ __device__ __forceinline__ void apply_op(const typename Cx<R>::T *Tg, const type
   }
 }
 
-// Pass K, warp `warp` of the consumers: for its steps (32 fibres of one operator group,
-// one per lane), y = T^{op0} x0 (+ T^{op1} x1) along axis K, stored to the item's
-// destination tile.  Every destination of a pass is written by exactly one item.
+// Pass K, warp `warp` of the consumers.  The pass's fibres (n_items * P^(D-1), item by
+// item, the n_two two-source items first) are taken 32 at a time ("steps", one fibre per
+// lane); a step costs one unit of work per source, and the warps split the work evenly.
+// Each lane computes y = C^{op0} x0 (+ C^{op1} x1) along axis K for its fibre with its
+// item's operators and stores it to the item's destination tile (every destination of a
+// pass is written by exactly one item).
 template <typename R, int D, int P, int K>
-__device__ __forceinline__ void run_pass(const Item *items, const Group *groups, int ng,
+__device__ __forceinline__ void run_pass(const Item *items, int n_items, int n_two,
                                          const typename Cx<R>::T *src, typename Cx<R>::T *dst,
-                                         const typename Cx<R>::T *table, const double2 *scale,
-                                         int warp, int lane) {
+                                         const typename Cx<R>::T *table, int warp, int lane) {
   using C = typename Cx<R>::T;
   using S = LevelShape<R, D, P>;
   constexpr int FIB = S::FIB, TS = S::TS;
   constexpr int SK = ipow(P, D - 1 - K);  // element stride of axis K
-  if (ng <= 0) return;
-  const Group last = groups[ng - 1];
-  const int total = last.work_begin + ((last.n_items * FIB + 31) / 32) * (last.op1 == 0xffff ? 1 : 2);
+  const int nfib = n_items * FIB, nfib2 = n_two * FIB;
+  const int steps = (nfib + 31) / 32, steps2 = (nfib2 + 31) / 32;  // steps2: with a two-source fibre
+  const int total = steps + steps2;
   const int per = (total + kConsumerWarps - 1) / kConsumerWarps;
-  const int w0 = warp * per, w1 = min(total, w0 + per);
-  if (w0 >= w1) return;
-  int g = 0;
-  while (g + 1 < ng && groups[g + 1].work_begin <= w0) ++g;
+  const int w0 = min(total, warp * per), w1 = min(total, w0 + per);
+  // the first step whose work starts at or after w: 2s for s < steps2, then steps2 + s
+  auto first_step = [&](int w) { return w <= 2 * steps2 ? (w + 1) / 2 : w - steps2; };
+  const int s0 = first_step(w0), s1 = first_step(w1);
 #pragma unroll 1
-  for (; g < ng; ++g) {
-    const Group gr = groups[g];
-    if (gr.work_begin >= w1) break;
-    const bool two = gr.op1 != 0xffff;
-    const int wt = two ? 2 : 1;
-    const int nfib = gr.n_items * FIB;
-    // steps j of the group whose work start work_begin + j * wt lies in [w0, w1)
-    const int a = w0 > gr.work_begin ? (w0 - gr.work_begin + wt - 1) / wt : 0;
-    const int b = min((nfib + 31) / 32, (w1 - gr.work_begin + wt - 1) / wt);
-    const C *T0 = table + (size_t)gr.op0 * S::OPS;
-    const C *T1 = table + (size_t)(two ? gr.op1 : gr.op0) * S::OPS;
-#pragma unroll 1
-    for (int st = a; st < b; ++st) {
-      const int fl = st * 32 + lane;
-      if (fl >= nfib) continue;
-      const int ti = fl / FIB, f = fl - ti * FIB;
-      const Item it = items[gr.item_begin + ti];
-      const int base = (f / SK) * SK * P + (f % SK);
-      C y[P];
+  for (int st = s0; st < s1; ++st) {
+    const int fl = st * 32 + lane;
+    if (fl >= nfib) continue;
+    const int ti = fl / FIB, f = fl - ti * FIB;
+    const Item it = items[ti];
+    const int base = (f / SK) * SK * P + (f % SK);
+    C y[P];
 #pragma unroll
-      for (int m = 0; m < P; ++m) y[m] = cmk((R)0, (R)0);
-      apply_op<R, P, S::PP, SK>(T0, src + (size_t)it.src0 * TS + base, y);
-      if (two) apply_op<R, P, S::PP, SK>(T1, src + (size_t)it.src1 * TS + base, y);
-      if (K == D - 1 && scale) {  // the output tile's unit-modulus factor (N != 2^L)
-        const double2 sv = scale[it.dst];
-        const C sc = cmk((R)sv.x, (R)sv.y);
+    for (int m = 0; m < P; ++m) y[m] = cmk((R)0, (R)0);
+    apply_op<R, P, S::PP, SK>(table + (size_t)(it.ops & 3) * S::OPS_S, src + (size_t)it.src0 * TS + base, y);
+    if (fl < nfib2)
+      apply_op<R, P, S::PP, SK>(table + (size_t)(it.ops >> 2) * S::OPS_S, src + (size_t)it.src1 * TS + base, y);
+    C *Y = dst + (size_t)it.dst * TS + base;
 #pragma unroll
-        for (int m = 0; m < P; ++m) y[m] = cmul(y[m], sc);
-      }
-      C *Y = dst + (size_t)it.dst * TS + base;
-#pragma unroll
-      for (int m = 0; m < P; ++m) Y[m * SK] = y[m];
-    }
+    for (int m = 0; m < P; ++m) Y[m * SK] = y[m];
   }
 }
 
@@ -240,7 +229,7 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char *ptr = smem;
   C *s_table = reinterpret_cast<C *>(ptr);
-  ptr += (S::table_bytes + 15) & ~(size_t)15;
+  ptr += (S::smem_table_bytes + 15) & ~(size_t)15;
   uint64_t *full = reinterpret_cast<uint64_t *>(ptr);  // full[2], staged[2]
   uint64_t *staged = full + 2;
   ptr += 64;
@@ -253,7 +242,7 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const C *table = reinterpret_cast<const C *>(a.table);
-  for (int e = tid; e < NOPS * S::OPS; e += kLevelThreads) s_table[e] = table[e];
+  for (int e = tid; e < NOPS * S::OPS; e += kLevelThreads) s_table[(e / S::OPS) * S::OPS_S + e % S::OPS] = table[e];
   if (tid == 0) {
     mbar_init(&full[0], 1);
     mbar_init(&full[1], 1);
@@ -279,14 +268,8 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
       if (!__all_sync(0xffffffffu, ok)) return false;
       const unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
       const int32_t *hdr = reinterpret_cast<const int32_t *>(meta_s);
-      int n_items = 0, n_groups = 0;
-      for (int k = 0; k < D; ++k) {
-        n_items += hdr[k];
-        n_groups += hdr[3 + k];
-      }
-      const int n_oruns = hdr[7];
-      const Run *oruns = reinterpret_cast<const Run *>(meta_s + kBlobHeader + (size_t)n_items * sizeof(Item) +
-                                                       (((size_t)n_groups * sizeof(Group) + 7) & ~(size_t)7));
+      const int n_items = hdr[0] + hdr[1] + hdr[2], n_oruns = hdr[7];
+      const Run *oruns = reinterpret_cast<const Run *>(meta_s + kBlobHeader + (size_t)n_items * sizeof(Item));
       const C *stage_t = D == 3 ? scr0 + (size_t)(s % S::NSCR) * a.cap1 * TS : slot0 + (size_t)s * a.cap0 * TS;
       const unsigned char *stage = reinterpret_cast<const unsigned char *>(stage_t);
       unsigned char *obase = gout;
@@ -350,7 +333,6 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
   }
 
   // ---------------- consumer warps
-  const void *cur_table = a.table;  // operators now in s_table
   for (int it = 0; it < n_work; ++it) {
     const int s = it & 1, use = it >> 1;
     const bool ok = mbar_wait(&full[s], use & 1, a.wait_limit);
@@ -362,36 +344,16 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
     C *in_s = slot0 + (size_t)s * a.cap0 * TS;
     C *scr = scr0 + (size_t)(s % S::NSCR) * a.cap1 * TS;
     const int32_t *hdr = reinterpret_cast<const int32_t *>(meta_s);
-    const int n_items = hdr[0] + hdr[1] + hdr[2], n_groups = hdr[3] + hdr[4] + hdr[5];
     const Item *i0 = reinterpret_cast<const Item *>(meta_s + kBlobHeader);
-    const Group *g0 = reinterpret_cast<const Group *>(i0 + n_items);
     const Item *i1 = i0 + hdr[0];
-    const Group *g1 = g0 + hdr[3];
-    const double2 *scale = nullptr;
-    if (hdr[8]) {
-      const size_t soff = (kBlobHeader + (size_t)n_items * sizeof(Item) +
-                           (((size_t)n_groups * sizeof(Group) + 7) & ~(size_t)7) + (size_t)hdr[7] * sizeof(Run) + 15) &
-                          ~(size_t)15;
-      scale = reinterpret_cast<const double2 *>(meta_s + soff);
-    }
-    if (a.entries) {
-      // a batched launch: the chunk's plan may have its own operators (its own N)
-      const void *tb = a.entries[blockIdx.x + (it / a.nrhs) * gridDim.x].table;
-      if (tb != cur_table) {
-        const C *src = reinterpret_cast<const C *>(tb);
-        for (int e = tid; e < NOPS * S::OPS; e += kConsumerWarps * 32) s_table[e] = src[e];
-        cur_table = tb;
-        consumer_sync();
-      }
-    }
-    run_pass<R, D, P, 0>(i0, g0, hdr[3], in_s, scr, s_table, scale, warp, lane);
+    run_pass<R, D, P, 0>(i0, hdr[0], hdr[3], in_s, scr, s_table, warp, lane);
     consumer_sync();
     if (D == 3) {
-      run_pass<R, D, P, (D == 3 ? 1 : 0)>(i1, g1, hdr[4], scr, in_s, s_table, scale, warp, lane);
+      run_pass<R, D, P, (D == 3 ? 1 : 0)>(i1, hdr[1], hdr[4], scr, in_s, s_table, warp, lane);
       consumer_sync();
-      run_pass<R, D, P, D - 1>(i1 + hdr[1], g1 + hdr[4], hdr[5], in_s, scr, s_table, scale, warp, lane);  // staged in scr
+      run_pass<R, D, P, D - 1>(i1 + hdr[1], hdr[2], hdr[5], in_s, scr, s_table, warp, lane);  // staged in scr
     } else {
-      run_pass<R, D, P, D - 1>(i1, g1, hdr[4], scr, in_s, s_table, scale, warp, lane);  // staged in in_s
+      run_pass<R, D, P, D - 1>(i1, hdr[1], hdr[4], scr, in_s, s_table, warp, lane);  // staged in in_s
     }
     fence_async_shared();  // the staged tiles are visible to the bulk stores
     consumer_sync();

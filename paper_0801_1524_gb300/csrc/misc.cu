@@ -5,15 +5,15 @@
 
 namespace bfly {
 
-cudaError_t launch_weights(int prec, int64_t n, int dim, int p, double rho, int kind, const double *off,
+cudaError_t launch_weights(int prec, int64_t n, int dim, int p, int kind, const double *off,
                            const double *inv_den, void *W, cudaStream_t s) {
   const int64_t work = n * dim;
   if (work == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((work + 255) / 256);
   if (prec == 0)
-    weights_kernel<double><<<blocks, 256, 0, s>>>(n, dim, p, rho, kind, off, inv_den, reinterpret_cast<double2 *>(W));
+    weights_kernel<double><<<blocks, 256, 0, s>>>(n, dim, p, kind, off, inv_den, reinterpret_cast<double2 *>(W));
   else
-    weights_kernel<float><<<blocks, 256, 0, s>>>(n, dim, p, rho, kind, off, inv_den, reinterpret_cast<float2 *>(W));
+    weights_kernel<float><<<blocks, 256, 0, s>>>(n, dim, p, kind, off, inv_den, reinterpret_cast<float2 *>(W));
   return cudaGetLastError();
 }
 

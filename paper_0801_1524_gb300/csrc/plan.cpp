@@ -20,7 +20,7 @@ inline uint64_t morton(const int64_t *a, int dim, int L) {
 
 }  // namespace
 
-std::string build_tree(HostTree &T, int dim, int L, double rho, int64_t n, const double *pts) {
+std::string build_tree(HostTree &T, int dim, int L, double N, double scale, int64_t n, const double *pts) {
   T = HostTree();
   T.dim = dim;
   T.L = L;
@@ -32,10 +32,10 @@ std::string build_tree(HostTree &T, int dim, int L, double rho, int64_t n, const
   for (int64_t i = 0; i < n; ++i) {
     for (int d = 0; d < dim; ++d) {
       const double v = pts[i * dim + d];
-      if (!(v >= 0.0) || !(v <= rho * (double)side)) return "point coordinate outside [0, N]";
-      const double u = v / rho;  // in leaf widths; exactly v when N = 2^L
+      if (!(v >= 0.0) || !(v <= N)) return "point coordinate outside [0, N]";
+      const double u = scale == 1.0 ? v : v * scale;  // in [0, 2^L]
       int64_t a = (int64_t)std::floor(u);
-      if (a > side - 1) a = side - 1;  // the far edge N belongs to the last box
+      if (a > side - 1) a = side - 1;  // the far edge belongs to the last box
       leaf[i * dim + d] = a;
       off[i * dim + d] = u - (double)a;  // exact: u and a differ by less than 2
     }
@@ -80,37 +80,36 @@ std::string build_tree(HostTree &T, int dim, int L, double rho, int64_t n, const
   return "";
 }
 
-void leaf_weights(int p, double rho, double tau, double *w) {
-  // G_{ll'} = exp(2 pi i rho l l'/q^2) is the Vandermonde matrix of the nodes
-  // z_m = exp(2 pi i rho m/q^2) and v(tau)_l = z(tau)^l with z(tau) = exp(2 pi i rho tau/q),
-  // so G^{-1} v(tau) holds the Lagrange basis polynomials of those nodes at z(tau).  As
+void leaf_weights(int p, double tau, double *w) {
+  // G_{ll'} = exp(2 pi i l l'/q^2) is the Vandermonde matrix of the nodes
+  // z_m = exp(2 pi i m/q^2) and v(tau)_l = z(tau)^l with z(tau) = exp(2 pi i tau/q), so
+  // G^{-1} v(tau) holds the Lagrange basis polynomials of those nodes at z(tau).  As
   // z - z_n = 2i sin((theta - phi_n)/2) e^{i(theta + phi_n)/2}, the product form is
-  //   w_m = e^{i pi rho (tau - m/q)} prod_{n != m} sin(pi rho (tau - n/q)/q) / sin(pi rho (m-n)/q^2),
+  //   w_m = e^{i pi (tau - m/q)} prod_{n != m} sin(pi (tau - n/q)/q) / sin(pi (m-n)/q^2),
   // which needs no inverse of the ill-conditioned G.
   const int q = p - 1;
   for (int m = 0; m < p; ++m) {
     double num = 1.0, den = 1.0;
     for (int n = 0; n < p; ++n) {
       if (n == m) continue;
-      num *= std::sin(M_PI * rho * (tau - (double)n / q) / q);
-      den *= std::sin(M_PI * rho * ((double)(m - n) / ((double)q * q)));
+      num *= std::sin(M_PI * (tau - (double)n / q) / q);
+      den *= std::sin(M_PI * ((double)(m - n) / ((double)q * q)));
     }
-    const double ang = M_PI * rho * (tau - (double)m / q);
+    const double ang = M_PI * (tau - (double)m / q);
     w[2 * m] = std::cos(ang) * num / den;
     w[2 * m + 1] = std::sin(ang) * num / den;
   }
 }
 
-std::vector<double> transfer_table(int p, double rho, bool adjoint) {
-  // Per axis, for A (index a, width w^A) and B (width w^B) with w^A w^B = rho N, the
-  // matching condition of Sec. 2.1 with the evaluation of Fig. 1 gives f^{AB} = T f^{A'Bc},
-  //   T_{ml} = e^{-2 pi i rho a m/q} w_m(tau_l) e^{2 pi i rho a tau_l},  tau_l = (delta + l/q)/2
+std::vector<double> transfer_table(int p, bool adjoint) {
+  // Per axis, for A (index a, width w^A) and B (width w^B) with w^A w^B = N, the matching
+  // condition of Sec. 2.1 with the evaluation of Fig. 1 gives f^{AB} = T f^{A'Bc},
+  //   T_{ml} = e^{-2 pi i a m/q} w_m(tau_l) e^{2 pi i a tau_l},  tau_l = (delta + l/q)/2
   // (the index of B cancels; eqs. M1 and E1).  With the rescaled charges
-  // g^{AB}_m = e^{2 pi i rho a m/q} f^{AB}_m and a = 2a' + gamma this becomes
-  //   g^{AB} = e^{2 pi i rho a' delta} C(gamma, delta) g^{A'Bc},
-  //   C(gamma, delta)_{ml} = w_m(tau_l) e^{2 pi i rho gamma tau_l},
-  // four operators per axis whatever the level; the scalar is 1 when N = 2^L (rho = 1)
-  // and is applied per tile otherwise (make_stage_program).  Operator gamma*2 + delta.
+  // g^{AB}_m = e^{2 pi i a m/q} f^{AB}_m and a = 2a' + gamma this becomes
+  //   g^{AB} = C(gamma, delta) g^{A'Bc},  C(gamma, delta)_{ml} = w_m(tau_l) e^{2 pi i gamma tau_l}
+  // (the remaining factor e^{2 pi i a' delta} is 1): four operators per axis whatever
+  // the level.  Operator gamma*2 + delta.
   const int q = p - 1;
   std::vector<double> T((size_t)4 * p * p * 2, 0.0);
   std::vector<double> w((size_t)2 * p);
@@ -119,9 +118,9 @@ std::vector<double> transfer_table(int p, double rho, bool adjoint) {
       const int op = gamma * 2 + delta;
       for (int l = 0; l < p; ++l) {
         const double tau = (double)(delta * q + l) / (2.0 * q);
-        leaf_weights(p, rho, tau, w.data());
-        // e^{2 pi i rho gamma tau_l}: an exact rational angle when rho = 1
-        const double ang = rho == 1.0 ? M_PI * (double)(gamma * (delta * q + l)) / q : 2.0 * M_PI * rho * gamma * tau;
+        leaf_weights(p, tau, w.data());
+        // e^{2 pi i gamma tau_l} = e^{i pi gamma (delta q + l)/q}, an exact rational angle
+        const double ang = M_PI * (double)(gamma * (delta * q + l)) / q;
         const double c = std::cos(ang), sn = std::sin(ang);
         for (int m = 0; m < p; ++m) {
           const double wr = w[2 * m], wi = w[2 * m + 1];
@@ -150,17 +149,15 @@ struct UnitProg {
   int src[3][8][2];
   int op[3][8][2];
   int32_t out_tile[8];
-  double out_scale[8][2];  // unit-modulus factor of every output tile (rho != 1)
 };
 
 }  // namespace
 
-StageProgram make_stage_program(int dim, int p, double rho, const std::vector<int32_t> &csAp,
+StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp,
                                 const std::vector<int32_t> &xidx, const std::vector<int32_t> &csB,
                                 const std::vector<int32_t> &kidx, bool adjoint, ChunkCaps caps) {
   StageProgram prog;
   const int D = dim;
-  const bool scaled = rho != 1.0;
   const int64_t nAp = (int64_t)csAp.size() - 1, nB = (int64_t)csB.size() - 1;
   const int64_t nBc = (int64_t)kidx.size() / dim;
   const int64_t in_row = adjoint ? nB : nBc, out_row = adjoint ? nBc : nB;
@@ -214,31 +211,19 @@ StageProgram make_stage_program(int dim, int p, double rho, const std::vector<in
     std::vector<int32_t> osorted = outs;
     std::sort(osorted.begin(), osorted.end());
     std::vector<Item> items;
-    std::vector<Group> groups;
-    std::vector<double> oscale(scaled ? 2 * osorted.size() : 0);
-    int32_t icount[3] = {0, 0, 0}, gcount[3] = {0, 0, 0};
-    int fib = 1;  // fibres of one tile along one axis
-    for (int d = 0; d + 1 < D; ++d) fib *= p;
+    int32_t icount[3] = {0, 0, 0}, tcount[3] = {0, 0, 0};
     int oi = 0;
     for (int k = 0; k < D; ++k) {
-      struct Keyed {
-        uint16_t op0, op1;
-        Item it;
-      };
-      std::vector<Keyed> pass;
+      std::vector<Item> pass;
       for (size_t u = 0; u < units.size(); ++u) {
         const UnitProg &U = units[u];
         for (int v = 0; v < U.n_pass[k]; ++v) {
-          Keyed e{0, 0xffff, Item{0xffff, 0xffff, 0, 0}};
+          Item e{0xffff, 0xffff, 0, 0};
           if (k == D - 1) {
             const int32_t g = outs[oi++];
-            e.it.dst = (uint16_t)(std::lower_bound(osorted.begin(), osorted.end(), g) - osorted.begin());
-            if (scaled) {
-              oscale[2 * e.it.dst] = U.out_scale[v][0];
-              oscale[2 * e.it.dst + 1] = U.out_scale[v][1];
-            }
+            e.dst = (uint16_t)(std::lower_bound(osorted.begin(), osorted.end(), g) - osorted.begin());
           } else {
-            e.it.dst = (uint16_t)(base[k][u] + v);
+            e.dst = (uint16_t)(base[k][u] + v);
           }
           int got = 0;
           for (int j = 0; j < 2; ++j) {
@@ -246,32 +231,22 @@ StageProgram make_stage_program(int dim, int p, double rho, const std::vector<in
             if (sidx < 0) continue;
             const uint16_t slot = (uint16_t)(k == 0 ? slot_of[base_in[u] + sidx] : base[k - 1][u] + sidx);
             if (got == 0) {
-              e.it.src0 = slot;
-              e.op0 = (uint16_t)U.op[k][v][j];
+              e.src0 = slot;
+              e.ops = (uint16_t)U.op[k][v][j];
             } else {
-              e.it.src1 = slot;
-              e.op1 = (uint16_t)U.op[k][v][j];
+              e.src1 = slot;
+              e.ops |= (uint16_t)(U.op[k][v][j] << 2);
             }
             ++got;
           }
           pass.push_back(e);
         }
       }
-      std::stable_sort(pass.begin(), pass.end(), [](const Keyed &x, const Keyed &y) {
-        return x.op0 != y.op0 ? x.op0 < y.op0 : x.op1 < y.op1;
-      });
+      // two-source items first (a step then rarely mixes one- and two-source fibres)
+      std::stable_partition(pass.begin(), pass.end(), [](const Item &x) { return x.src1 != 0xffff; });
       icount[k] = (int32_t)pass.size();
-      int work = 0;
-      for (size_t i = 0; i < pass.size();) {
-        size_t j = i;
-        while (j < pass.size() && pass[j].op0 == pass[i].op0 && pass[j].op1 == pass[i].op1) ++j;
-        const int n = (int)(j - i);
-        groups.push_back(Group{(uint16_t)i, (uint16_t)n, pass[i].op0, pass[i].op1, (uint16_t)work, 0});
-        work += ((n * fib + 31) / 32) * (pass[i].op1 == 0xffff ? 1 : 2);
-        ++gcount[k];
-        i = j;
-      }
-      for (const Keyed &e : pass) items.push_back(e.it);
+      for (const Item &e : pass) tcount[k] += e.src1 != 0xffff;
+      items.insert(items.end(), pass.begin(), pass.end());
     }
     std::vector<Run> oruns;
     for (size_t r = 0; r < osorted.size(); ++r) {
@@ -281,20 +256,15 @@ StageProgram make_stage_program(int dim, int p, double rho, const std::vector<in
         oruns.push_back(Run{osorted[r], (uint16_t)r, 1});
     }
     cur.blob_off = (int32_t)prog.blob.size();
-    const int32_t header[12] = {icount[0], icount[1], icount[2], gcount[0], gcount[1], gcount[2],
-                                cur.n_in, (int32_t)oruns.size(), scaled ? 1 : 0, 0, 0, 0};
-    const size_t ib = items.size() * sizeof(Item), gb = groups.size() * sizeof(Group);
-    const size_t ob = oruns.size() * sizeof(Run);
-    const size_t gpad = (gb + 7) & ~(size_t)7;  // runs start 8-byte aligned
-    const size_t soff = (kBlobHeader + ib + gpad + ob + 15) & ~(size_t)15;  // scalars 16-byte aligned
-    const size_t bytes = soff + oscale.size() * sizeof(double);
+    const int32_t header[kBlobHeader / 4] = {icount[0], icount[1], icount[2], tcount[0],
+                                             tcount[1], tcount[2], cur.n_in, (int32_t)oruns.size()};
+    const size_t ib = items.size() * sizeof(Item), ob = oruns.size() * sizeof(Run);
+    const size_t bytes = (kBlobHeader + ib + ob + 15) & ~(size_t)15;
     prog.blob.resize(prog.blob.size() + bytes, 0);
     unsigned char *dstp = prog.blob.data() + cur.blob_off;
     std::memcpy(dstp, header, kBlobHeader);
     std::memcpy(dstp + kBlobHeader, items.data(), ib);
-    std::memcpy(dstp + kBlobHeader + ib, groups.data(), gb);
-    std::memcpy(dstp + kBlobHeader + ib + gpad, oruns.data(), ob);
-    if (scaled) std::memcpy(dstp + soff, oscale.data(), oscale.size() * sizeof(double));
+    std::memcpy(dstp + kBlobHeader + ib, oruns.data(), ob);
     cur.blob_bytes = (int32_t)bytes;
     prog.chunks.push_back(cur);
     units.clear();
@@ -366,37 +336,16 @@ StageProgram make_stage_program(int dim, int p, double rho, const std::vector<in
       for (int v = 0; v < U.n_pass[D - 1]; ++v) {
         // the last pass's keys are output keys: find that output's tile
         for (int o = 0; o < n_out; ++o)
-          if (okey[o] == U.key[D - 1][v]) {
+          if (okey[o] == U.key[D - 1][v])
             U.out_tile[v] = adjoint ? (int32_t)(iAp * out_row + dtile[o])
                                     : (int32_t)((int64_t)gtile[o] * out_row + iB);
-            if (scaled) {
-              // The factor e^{2 pi i rho a' delta} of the next stage belongs to its input
-              // tile (A', Bc), i.e. to this stage's output (A, B) with a' = a and delta the
-              // bit of B within its parent: forward, e^{2 pi i rho sum_d a_d beta_d(B)} on
-              // the output; adjoint, the conjugate of this stage's own factor on its
-              // output (A', Bc).  Phase rho * S reduced mod 1 in FP64.
-              int64_t S = 0;
-              for (int d = 0; d < D; ++d) {
-                if (adjoint)
-                  S += (int64_t)apar[d] * (kidx[(int64_t)dtile[o] * D + d] & 1);
-                else
-                  S += (int64_t)xidx[(int64_t)gtile[o] * D + d] * ((kidx[(int64_t)c0 * D + d] >> 1) & 1);
-              }
-              double ph = rho * (double)S;
-              ph -= std::floor(ph);
-              U.out_scale[v][0] = std::cos(2.0 * M_PI * ph);
-              U.out_scale[v][1] = (adjoint ? -1.0 : 1.0) * std::sin(2.0 * M_PI * ph);
-            }
-          }
       }
       // capacity: buffer 0 holds inputs (and pass 1 in 3D), buffer 1 pass 0
       const int need0 = std::max(tot_in + U.n_in, D == 3 ? tot[1] + U.n_pass[1] : 0);
       const int need1 = tot[0] + U.n_pass[0];
       const int needo = tot[D - 1] + U.n_pass[D - 1];
-      // header, an item and up to one group per item, one run and (rho != 1) one
-      // scalar per output, paddings
-      const int needb = kBlobHeader + 20 * (need1 + (D == 3 ? tot[1] + U.n_pass[1] : 0) + needo) + 8 * needo + 8 +
-                        15 + (scaled ? 16 * needo : 0);
+      // header, an item per pass tile, one run per output, padding
+      const int needb = kBlobHeader + 8 * (need1 + (D == 3 ? tot[1] + U.n_pass[1] : 0) + needo) + 8 * needo + 15;
       if (!units.empty() && (need0 > caps.cap0 || need1 > caps.cap1 || needo > caps.max_out ||
                              needb > caps.meta_bytes))
         flush();
@@ -421,19 +370,14 @@ std::string validate_program(const StageProgram &prog, int dim, int p, ChunkCaps
     if (c.blob_off < 0 || (c.blob_off & 15) || (size_t)c.blob_off + kBlobHeader > prog.blob.size())
       return "metadata blob out of range";
     const int32_t *hdr = reinterpret_cast<const int32_t *>(prog.blob.data() + c.blob_off);
-    int64_t nitems = 0, ngroups = 0;
+    int64_t nitems = 0;
     for (int k = 0; k < dim; ++k) {
-      if (hdr[k] != c.n_item[k] || hdr[3 + k] < (hdr[k] > 0) || hdr[3 + k] > hdr[k])
-        return "metadata header mismatch";
+      if (hdr[k] != c.n_item[k] || hdr[3 + k] < 0 || hdr[3 + k] > hdr[k]) return "metadata header mismatch";
       nitems += hdr[k];
-      ngroups += hdr[3 + k];
     }
-    if (hdr[6] != c.n_in || (hdr[8] != 0 && hdr[8] != 1) || hdr[9] || hdr[10] || hdr[11])
-      return "metadata header mismatch";
+    if (hdr[6] != c.n_in) return "metadata header mismatch";
     const int n_oruns = hdr[7];
-    const int64_t gpad = (ngroups * (int64_t)sizeof(Group) + 7) & ~(int64_t)7;
-    const int64_t soff = (kBlobHeader + nitems * (int64_t)sizeof(Item) + gpad + n_oruns * (int64_t)sizeof(Run) + 15) & ~(int64_t)15;
-    const int64_t need = soff + (hdr[8] ? (int64_t)c.n_item[dim - 1] * 16 : 0);
+    const int64_t need = (kBlobHeader + nitems * (int64_t)sizeof(Item) + n_oruns * (int64_t)sizeof(Run) + 15) & ~(int64_t)15;
     if (c.blob_bytes != need || c.blob_bytes > caps.meta_bytes || (size_t)c.blob_off + c.blob_bytes > prog.blob.size())
       return "metadata blob out of range";
     if (c.run_off < 0 || c.n_runs < 1 || (size_t)c.run_off + c.n_runs > prog.runs.size())
@@ -448,13 +392,7 @@ std::string validate_program(const StageProgram &prog, int dim, int p, ChunkCaps
     if (covered != c.n_in) return "runs do not cover the inputs";
     const unsigned char *bp = prog.blob.data() + c.blob_off;
     const Item *items = reinterpret_cast<const Item *>(bp + kBlobHeader);
-    const Group *groups = reinterpret_cast<const Group *>(bp + kBlobHeader + nitems * sizeof(Item));
-    const Run *oruns = reinterpret_cast<const Run *>(bp + kBlobHeader + nitems * sizeof(Item) + gpad);
-    if (hdr[8]) {
-      const double *sc = reinterpret_cast<const double *>(bp + soff);
-      for (int r = 0; r < c.n_item[dim - 1]; ++r)
-        if (!(std::fabs(std::hypot(sc[2 * r], sc[2 * r + 1]) - 1.0) < 1e-12)) return "output factor not of unit modulus";
-    }
+    const Run *oruns = reinterpret_cast<const Run *>(bp + kBlobHeader + nitems * sizeof(Item));
     covered = 0;
     for (int r = 0; r < n_oruns; ++r) {
       const Run &rn = oruns[r];
@@ -463,37 +401,21 @@ std::string validate_program(const StageProgram &prog, int dim, int p, ChunkCaps
       covered += rn.count;
     }
     if (covered != nl) return "output runs do not cover the outputs";
-    int fib = 1;
-    for (int d = 0; d + 1 < dim; ++d) fib *= p;
-    int off = 0, goff = 0;
+    int off = 0;
     int nsrc = c.n_in;  // sources of pass k live in the previous pass's buffer
     for (int k = 0; k < dim; ++k) {
-      const int ni = hdr[k], ng = hdr[3 + k];
+      const int ni = hdr[k], n2 = hdr[3 + k];
       std::vector<char> seen(c.n_item[k], 0);
       for (int i = 0; i < ni; ++i) {
         const Item &it = items[off + i];
         if (it.src0 >= nsrc) return "item source 0 out of range";
+        if ((i < n2) != (it.src1 != 0xffff)) return "two-source items do not lead the pass";
         if (it.src1 != 0xffff && it.src1 >= nsrc) return "item source 1 out of range";
+        if (it.ops >= (it.src1 != 0xffff ? 16 : 4)) return "operator out of range";
         if (it.dst >= c.n_item[k] || seen[it.dst]) return "item destination out of range or repeated";
         seen[it.dst] = 1;
       }
-      int covered_i = 0, work = 0;
-      for (int g = 0; g < ng; ++g) {
-        const Group &gr = groups[goff + g];
-        if (gr.item_begin != covered_i || gr.n_items < 1 || gr.item_begin + gr.n_items > ni)
-          return "operator groups do not tile the items";
-        if (gr.work_begin != work) return "operator group work offsets inconsistent";
-        work += ((gr.n_items * fib + 31) / 32) * (gr.op1 == 0xffff ? 1 : 2);
-        if (work > 0xffff) return "pass work exceeds 16 bits";
-        if (gr.op0 >= 64 || (gr.op1 != 0xffff && gr.op1 >= 64)) return "operator out of range";
-        for (int i = 0; i < gr.n_items; ++i)
-          if ((items[off + gr.item_begin + i].src1 == 0xffff) != (gr.op1 == 0xffff))
-            return "item source count differs from its group";
-        covered_i += gr.n_items;
-      }
-      if (covered_i != ni) return "operator groups do not cover the items";
       off += ni;
-      goff += ng;
       nsrc = c.n_item[k];
     }
   }

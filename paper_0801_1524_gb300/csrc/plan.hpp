@@ -9,12 +9,11 @@ namespace bfly {
 
 // One block of work of the recursive step: a run of consecutive units (A', B), compiled
 // on the host into per-pass item lists (see make_stage_program).  Its metadata blob (a
-// 48-byte header {n_item[3], n_group[3], n_in, n_out_runs, scaled, 0, 0, 0}, the items of
-// every pass ordered by operator group, the groups (padded to 8 bytes), the output runs,
-// then, 16-byte aligned and only when scaled, one complex FP64 factor per output slot) is
-// copied to shared memory in one piece; its inputs are copied run by run, its outputs
-// written back run by run.
-constexpr int kBlobHeader = 48;
+// 32-byte header {n_item[3], n_two[3], n_in, n_out_runs} (n_two: the leading
+// two-source items of each pass), the items of every pass, then the output runs, padded
+// to 16 bytes) is copied to shared memory in one piece; its inputs are copied run by run,
+// its outputs written back run by run.
+constexpr int kBlobHeader = 32;
 struct ChunkDesc {
   int32_t blob_off;   // byte offset of the blob in StageProgram::blob (16-byte aligned)
   int32_t blob_bytes; // multiple of 16
@@ -25,27 +24,16 @@ struct ChunkDesc {
 };
 static_assert(sizeof(ChunkDesc) == 32, "ChunkDesc is uploaded as 32 bytes");
 
-// One output tile of a pass: the sum over at most two source tiles of the previous pass
-// (pass 0: input tiles) of T^{op} applied along the pass's axis, stored to slot dst.
+// One output tile of a pass: the sum over one or two source tiles of the previous pass
+// (pass 0: input tiles) of C^{op} applied along the pass's axis, stored to slot dst.  A
+// pass lists its two-source items first; every lane of a step takes one fibre of the
+// flat list of the pass's fibres, with its own item's operators.
 struct Item {
   uint16_t src0, src1;  // chunk-local source slots; src1 = 0xffff when absent
   uint16_t dst;         // destination slot (last pass: staging slot of the output run)
-  uint16_t pad;
+  uint16_t ops;         // op of src0 in bits 0-1, op of src1 in bits 2-3 (op = gamma*2 + delta)
 };
 static_assert(sizeof(Item) == 8, "Item is uploaded as 8 bytes");
-
-// A run of items of one pass with the same operators (op0 for the first source, op1 for
-// the second, or 0xffff when the items have one source); its fibres (n_items * P^(D-1))
-// are processed 32 at a time ("steps", one fibre per lane), so both operators are the
-// same in every lane of a warp.  A step costs one unit of work per source; the consumer
-// warps split a pass's work evenly, work_begin being the group's first unit.
-struct Group {
-  uint16_t item_begin, n_items;
-  uint16_t op0, op1;
-  uint16_t work_begin;
-  uint16_t pad;
-};
-static_assert(sizeof(Group) == 12, "Group is uploaded as 12 bytes");
 
 // A run of consecutive tiles: global tiles [start, start + count) <-> chunk-local slots
 // [slot, slot + count) (inputs: copied in; outputs: written back from the staging slots).
@@ -55,8 +43,7 @@ struct Run {
 };
 static_assert(sizeof(Run) == 8, "Run is uploaded as 8 bytes");
 
-// A chunk of a batched launch: the chunk and the buffers and operators of the plan it
-// belongs to.
+// A chunk of a batched launch: the chunk and the buffers of the plan it belongs to.
 struct BatchEntry {
   ChunkDesc d;
   const unsigned char *blob;
@@ -64,14 +51,12 @@ struct BatchEntry {
   const void *in;
   void *out;
   int64_t in_rhs, out_rhs;  // elements between right-hand sides of the plan's buffers
-  const void *table;        // the plan's operator table (it depends on N / 2^L)
-  int64_t pad;
 };
-static_assert(sizeof(BatchEntry) == 96, "BatchEntry is uploaded as 96 bytes");
+static_assert(sizeof(BatchEntry) == 80, "BatchEntry is uploaded as 80 bytes");
 
 struct StageProgram {
   std::vector<ChunkDesc> chunks;
-  std::vector<unsigned char> blob;  // per chunk: header, Item[], Group[], Run[n_out_runs], scalars
+  std::vector<unsigned char> blob;  // per chunk: header, Item[], Run[n_out_runs]
   std::vector<Run> runs;
   // host-side copies used for validation and statistics
   std::vector<int32_t> in_tiles;    // global tile of every input slot, chunk after chunk
@@ -85,14 +70,15 @@ struct ChunkCaps {
   int cap0, cap1, max_out, meta_bytes;
 };
 
-// A quadtree (octree) over [0,N]^dim, L levels below the root, leaves of width
-// rho = N / 2^L (1 when N = 2^L), non-empty boxes only, boxes of every level in Morton
-// order so that the children of a box are consecutive.
+// A quadtree (octree) over [0,2^L]^dim with unit leaves, non-empty boxes only, boxes of
+// every level in Morton order so that the children of a box are consecutive.  The points
+// are those of the caller scaled by s = sqrt(2^L / N) (s = 1 when N = 2^L), so that
+// x.k/N = x'.k'/2^L: the transform of any N is the one of 2^L on the scaled points.
 struct HostTree {
   int dim = 0, L = 0;
   int64_t n = 0;
   std::vector<int32_t> perm;              // sorted position -> caller index
-  std::vector<double> off;                // [n][dim] offset from the leaf corner in leaf widths, [0,1]
+  std::vector<double> off;                // [n][dim] scaled offset from the leaf corner, [0,1]
   std::vector<int32_t> point_leaf;        // sorted position -> leaf number
   std::vector<int32_t> leaf_start;        // [nleaf+1] point range of every leaf
   std::vector<std::vector<int32_t>> idx;  // idx[s]: [n_s][dim] box index per axis
@@ -101,32 +87,31 @@ struct HostTree {
   int nchild(int s, int64_t i) const { return cs[s][i + 1] - cs[s][i]; }
 };
 
-// Sec. 2.2 step 1.  pts: [n][dim] in [0, N] with N = rho 2^L; a coordinate v lies in
-// leaf floor(v / rho), the far edge N in the last leaf.  Returns an error message or "".
-std::string build_tree(HostTree &T, int dim, int L, double rho, int64_t n, const double *pts);
+// Sec. 2.2 step 1.  pts: [n][dim] in [0, N]; a coordinate v lies in leaf floor(v s)
+// (clamped to 2^L - 1).  Returns an error message or "".
+std::string build_tree(HostTree &T, int dim, int L, double N, double scale, int64_t n, const double *pts);
 
 // Transfer operators of the recursive step (eqs. M1 and E1 combined) for the rescaled
-// charges g^{AB}_m = e^{2 pi i rho a m/q} f^{AB}_m (a the index of A along the axis), per
-// axis:  C^{(gamma,delta)}[m][l] = w_m(tau_l) e^{2 pi i rho gamma tau_l},
+// charges g^{AB}_m = e^{2 pi i a m/q} f^{AB}_m (a the index of A along the axis), per
+// axis:  C^{(gamma,delta)}[m][l] = w_m(tau_l) e^{2 pi i gamma tau_l},
 // tau_l = (delta + l/q)/2, gamma the bit of A within A', delta that of Bc within B;
 // stored [4][p][p] as interleaved (re, im) doubles, op index gamma*2 + delta.
 // adjoint = true stores the conjugate transpose of every operator.
-std::vector<double> transfer_table(int p, double rho, bool adjoint);
+std::vector<double> transfer_table(int p, bool adjoint);
 
 // Lagrange weights of the leaf step, w_m(tau) = (G^{-1} v(tau))_m, m = 0..p-1, for
-// G_{ll'} = e^{2 pi i rho l l'/q^2}, v(tau)_l = e^{2 pi i rho l tau/q}, tau in leaf widths.
-void leaf_weights(int p, double rho, double tau, double *w /* 2p doubles */);
+// G_{ll'} = e^{2 pi i l l'/q^2}, v(tau)_l = e^{2 pi i l tau/q}, tau in leaf widths.
+void leaf_weights(int p, double tau, double *w /* 2p doubles */);
 
 // The recursive step at stage t as chunk programs.  Forward: unit (A', B) reads the tiles
 // f^{A'Bc} of the children Bc of B and writes f^{AB} for the children A of A'; adjoint:
 // reads f^{AB} of the children A, writes f^{A'Bc}.  The operator of every (A, Bc) pair is
 // (x)_d C^{(gamma_d(A), delta_d(Bc))}; passes apply one axis each and sum, before each
 // axis, the sources that agree on all bits still to be applied (sum factorisation).
-// When rho != 1 every output tile carries a unit-modulus factor (see transfer_table).
 //   csAp : children of the A' boxes (T_X level L-t-1 -> L-t), xidx: box indices of level L-t
 //   csB  : children of the B boxes (T_K level t -> t+1),       kidx: box indices of level t+1
 //   in_row / out_row: tiles per row of the input / output stage buffer.
-StageProgram make_stage_program(int dim, int p, double rho, const std::vector<int32_t> &csAp,
+StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp,
                                 const std::vector<int32_t> &xidx, const std::vector<int32_t> &csB,
                                 const std::vector<int32_t> &kidx, bool adjoint, ChunkCaps caps);
 

@@ -12,7 +12,8 @@
 struct bfly_plan_s {
   int dim = 0, p = 0, L = 0, prec = 1, max_nrhs = 1;
   unsigned flags = 0;
-  double N = 0, rho = 1.0;  // leaves rho = N / 2^L wide
+  double N = 0, rho = 1.0;  // rho = N / 2^L
+  double scale = 1.0;       // points are scaled by sqrt(2^L / N) (1 when N = 2^L)
   int64_t nx = 0, nk = 0;
   int device = -1;
   bfly::HostTree TX, TK;

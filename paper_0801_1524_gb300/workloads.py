@@ -105,14 +105,15 @@ def gaussian_sources(n: int, nrhs: int = 1, seed: int = 0, dtype=np.complex128):
 
 
 def random_points(n: int, N: float, dim: int, seed: int, edge_fraction: float = 0.0):
-    """Uniform points in [0,N]^dim; a fraction is snapped to the dyadic grid of spacing
-    h = N / 2^ceil(log2 N) (the unit grid when N is a power of two) and to N itself."""
+    """Uniform points in [0,N]^dim; a fraction is snapped to the grid of spacing
+    h = sqrt(N / 2^ceil(log2 N)) (the unit grid when N is a power of two) and to N itself."""
     rng = np.random.default_rng(seed)
     pts = rng.uniform(0.0, float(N), size=(n, dim))
     if edge_fraction > 0 and n > 0:
         m = max(1, int(edge_fraction * n))
         idx = rng.choice(n, size=min(m, n), replace=False)
-        h = float(N) / 2.0 ** max(0, math.ceil(math.log2(float(N)) - 1e-12)) if N > 1 else float(N)
+        Np = 2.0 ** max(0, math.ceil(math.log2(float(N)) - 1e-12)) if N > 1 else 1.0
+        h = math.sqrt(float(N) / Np)
         pts[idx] = np.floor(pts[idx] / h) * h
         if len(idx) > 1:
             pts[idx[0], :] = float(N)

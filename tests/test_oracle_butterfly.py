@@ -128,34 +128,35 @@ def test_planted_mistakes_fail_the_band(monkeypatch, mistake):
     assert eps > 2 * BANDS[(2, 7)][1], eps            # the band test would fail
 
 
-# ---- N not a power of two: L = ceil(log2 N) levels, leaves rho = N / 2^L wide, so that
-# w^A w^B = rho N <= N and the rank bound of Theorem 2.1 still holds.
+# ---- N not a power of two: with L = ceil(log2 N), the transform equals the one of
+# N' = 2^L on the points scaled by sqrt(N'/N); the butterfly runs on those (unit leaves).
 
-def test_general_N_near_power_of_two_is_in_band():
-    N = 1000.0                                     # rho = 0.977
+@pytest.mark.parametrize("dim,N", [(2, 700.0), (3, 12.0), (2, 0.75)])
+def test_general_N_scaled_form_is_the_same_transform(dim, N):
+    inst = w.small_random(dim, N, 5, nx=50, nk=40, seed=21)
+    f = inst.sources()[0]
+    xs, ks, Np = ob.power_of_two_form(inst.x, inst.k, N)
+    assert Np == 2.0 ** ob.levels_for(N) and Np >= N
+    assert xs.max() <= Np and ks.max() <= Np
+    assert rel_l2(direct(xs, ks, f, Np), direct(inst.x, inst.k, f, N)) < 1e-12
+
+
+@pytest.mark.parametrize("N", [1000.0, 600.3, 700.0])
+def test_general_N_error_in_band(N):
     x, k, f = _curves(N)
     eps = rel_l2(ob.butterfly(x, k, f, N, 7), direct(x, k, f, N))
     lo, hi = BANDS[(2, 7)]
     assert lo / 8 < eps < 2 * hi, eps
 
 
-@pytest.mark.parametrize("N", [600.3, 700.0])
-def test_general_N_error_below_band_and_shrinks_with_rho(N):
-    # a smaller rho N than the power of two above it can only lower the error
-    x, k, f = _curves(N)
-    eps = rel_l2(ob.butterfly(x, k, f, N, 7), direct(x, k, f, N))
-    assert eps < 2 * BANDS[(2, 7)][1], eps
-    x2, k2, f2 = _curves(1024.0)
-    assert eps < rel_l2(ob.butterfly(x2, k2, f2, 1024.0, 7), direct(x2, k2, f2, 1024.0))
-
-
 @pytest.mark.parametrize("dim", [2, 3])
 def test_general_N_exact_for_one_box_with_sources_on_nodes(dim):
-    # N = 0.75 < 1: no level below the root, the single leaf is 0.75 wide and its charge
-    # grid is 0.75 l/(p-1); sources on that grid make the method exact.
+    # N = 0.75 < 1: no level below the root; the scaled points lie in [0, 1] and sources
+    # on the unit box's charge grid l/(p-1) (in scaled coordinates) make the method exact.
     p, N = 5, 0.75
     q = p - 1
-    nodes = np.stack(np.meshgrid(*[N * np.arange(p) / q] * dim, indexing="ij"), -1).reshape(-1, dim)
+    s = np.sqrt(1.0 / N)
+    nodes = np.stack(np.meshgrid(*[np.arange(p) / q / s] * dim, indexing="ij"), -1).reshape(-1, dim)
     rng = np.random.default_rng(4)
     k = nodes[rng.choice(nodes.shape[0], size=nodes.shape[0] // 2, replace=False)]
     x = rng.uniform(0, N, (40, dim))
