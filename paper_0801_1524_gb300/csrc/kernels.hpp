@@ -10,8 +10,9 @@ namespace bfly {
 struct KernelSet {
   // recursive step at one stage; grid = persistent blocks, smem = dynamic bytes
   cudaError_t (*level)(const LevelArgs &a, bool adjoint, int grid, size_t smem, cudaStream_t s);
-  // raises the dynamic shared memory limit to the device maximum and returns the blocks
-  // per SM resident with `smem` bytes each
+  // raises the dynamic shared memory limit to the device maximum, writes the operator
+  // factors to constant memory (first call on a device) and returns the blocks per SM
+  // resident with `smem` bytes each
   cudaError_t (*level_setup)(size_t smem, int *blocks_per_sm);
   size_t (*level_smem)(const ChunkCaps &caps);
   int (*meta_bytes)(int cap0, int cap1, int max_out);

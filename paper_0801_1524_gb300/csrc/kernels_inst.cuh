@@ -1,5 +1,8 @@
 // Instantiates the kernel set for one p (BFLY_P) in its own translation unit, so that
 // the per-p files compile in parallel.
+#include <mutex>
+#include <vector>
+
 #include "kernels.hpp"
 #include "level.cuh"
 #include "points.cuh"
@@ -7,13 +10,62 @@
 namespace bfly {
 namespace {
 
+constexpr int kMaxDevices = 64;
+std::mutex g_ops_mutex;
+bool g_ops_ready[kMaxDevices][2] = {};  // [device][FP32?]
+
+// Writes the factors of the transfer operators of this p (both directions, FP64-built,
+// rounded once to the precision R) to constant memory of the current device, the first
+// time only: they are the same for every plan, so later plans find them in place.
+template <typename R>
+cudaError_t init_operators() {
+  using C = typename Cx<R>::T;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_ops_mutex);
+  bool &ready = g_ops_ready[dev][sizeof(R) == 4];
+  if (ready) return cudaSuccess;
+  constexpr int P = BFLY_P;
+  std::vector<C> w((size_t)2 * 2 * P * P), phi((size_t)2 * 2 * P);
+  std::vector<double> wd((size_t)2 * P * P * 2), pd((size_t)2 * P * 2);
+  for (int adj = 0; adj < 2; ++adj) {
+    transfer_factors(P, adj != 0, wd.data(), pd.data());
+    for (int i = 0; i < 2 * P * P; ++i) {
+      C c;
+      c.x = (R)wd[2 * i];
+      c.y = (R)wd[2 * i + 1];
+      w[(size_t)adj * 2 * P * P + i] = c;
+    }
+    for (int i = 0; i < 2 * P; ++i) {
+      C c;
+      c.x = (R)pd[2 * i];
+      c.y = (R)pd[2 * i + 1];
+      phi[(size_t)adj * 2 * P + i] = c;
+    }
+  }
+  if constexpr (sizeof(R) == 4) {
+    e = cudaMemcpyToSymbol(c_w32, w.data(), w.size() * sizeof(C));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_phi32, phi.data(), phi.size() * sizeof(C));
+  } else {
+    e = cudaMemcpyToSymbol(c_w64, w.data(), w.size() * sizeof(C));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_phi64, phi.data(), phi.size() * sizeof(C));
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) ready = true;
+  return e;
+}
+
 template <typename R, int D, int P>
 struct Impl {
   using S = LevelShape<R, D, P>;
   static cudaError_t level(const LevelArgs &a, bool adjoint, int grid, size_t smem, cudaStream_t s) {
-    (void)adjoint;  // the adjoint differs only in its program and operator table
     if (a.nchunks <= 0) return cudaSuccess;
-    level_kernel<R, D, P><<<grid, kLevelThreads, smem, s>>>(a);
+    if (adjoint)
+      level_kernel<R, D, P, true><<<grid, kLevelThreads, smem, s>>>(a);
+    else
+      level_kernel<R, D, P, false><<<grid, kLevelThreads, smem, s>>>(a);
     return cudaGetLastError();
   }
   static cudaError_t level_setup(size_t smem, int *blocks) {
@@ -25,9 +77,17 @@ struct Impl {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(level_kernel<R, D, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    e = cudaFuncSetAttribute(level_kernel<R, D, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(level_kernel<R, D, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) e = init_operators<R>();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, level_kernel<R, D, P>, kLevelThreads, smem);
+    int b2 = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, level_kernel<R, D, P, false>, kLevelThreads, smem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, level_kernel<R, D, P, true>, kLevelThreads, smem);
+    if (b2 < *blocks) *blocks = b2;
+    return e;
   }
   static size_t level_smem(const ChunkCaps &c) { return S::bytes(c); }
   static int meta_bytes(int cap0, int cap1, int max_out) { return S::meta_bytes(cap0, cap1, max_out); }
@@ -35,7 +95,8 @@ struct Impl {
     constexpr int PD = ipow(P, D);
     const int64_t work = a.nbox * PD;
     if (work == 0) return cudaSuccess;
-    dim3 grid((unsigned)((work + kPointThreads - 1) / kPointThreads), (unsigned)a.nrhs);
+    constexpr int64_t E = kPointThreads * kSpreadPerThread;
+    dim3 grid((unsigned)((work + E - 1) / E), (unsigned)a.nrhs);
     spread_kernel<R, D, P><<<grid, kPointThreads, 0, s>>>(a);
     return cudaGetLastError();
   }

@@ -18,11 +18,15 @@
 // slot, then copies chunk i's metadata blob and input tiles (runs of consecutive 16-byte
 // aligned tiles) into the slot with bulk copies completing on the slot's "full" mbarrier.
 // The consumer warps wait on "full" and run the passes.  A pass's fibres (two-source
-// items first) are taken 32 at a time ("steps", one fibre per lane), the warps split the
-// pass's work (one unit per source of a step) evenly, and every lane of a step computes
-// y = C^{op0} x0 (+ C^{op1} x1) for its fibre with its item's operators (four operators,
-// laid out so that any mix of them in a warp reads in one wavefront): P or 2P loads, P^2
-// or 2P^2 complex multiply-adds and P stores per fibre, one barrier per pass.  The last
+// items first, then ordered by operator) are taken 32 at a time ("steps", one fibre per
+// lane), the warps split the pass's work (one unit per source of a step) evenly, and
+// every lane of a step computes y = C^{op0} x0 (+ C^{op1} x1) for its fibre.  Each
+// operator is applied in its factored form C^{(gamma,delta)} = W(delta) diag(phi_gamma):
+// the lane's own diagonal (phi_0 = 1), then W(delta), whose entries live in constant
+// memory and enter the multiply-adds as constant-bank operands (delta is the same in
+// every lane of a step but at most one step per pass, where the two halves run one after
+// the other).  Per fibre: P (or 2P) shared-memory loads, P^2 (or 2P^2) complex
+// multiply-adds, P stores; one barrier per pass.  The last
 // pass stages its tiles in the slot; the consumers then signal
 // the slot's "staged" mbarrier and go on with the other slot, so that the write-back and
 // the next copies overlap their compute.  Every mbarrier wait gives up after a clock
@@ -52,30 +56,18 @@ struct LevelShape {
   static constexpr int PD = ipow(P, D);
   static constexpr int TS = tile_stride<R>(PD);
   static constexpr int FIB = PD / P;  // fibres of one tile along one axis
-  // FP32 operators are stored transposed, [op][l][m] with m padded to PP entries, so that
-  // one 16-byte load reads T[m][l] and T[m+1][l]; FP64 operators as [op][m][l]
-  static constexpr int PP = sizeof(R) == 4 ? (P + 1) & ~1 : P;
-  static constexpr int OPS = sizeof(R) == 4 ? P * PP : P * P;  // elements per operator
-  // In shared memory the operators are OPS_S elements apart, a stride of 8 (mod 32)
-  // words: the same entry of the four operators then lies in four different groups of
-  // banks, so that a warp whose lanes use different operators still reads them in one
-  // wavefront.
-  static constexpr int OPW = OPS * (int)(sizeof(C) / 4);  // words per operator
-  static constexpr int OPS_S = (OPW + ((8 - OPW % 32) + 32) % 32) / (int)(sizeof(C) / 4);
-  static constexpr size_t table_bytes = (size_t)NOPS * OPS * sizeof(C);  // global layout
-  static constexpr size_t smem_table_bytes = (size_t)NOPS * OPS_S * sizeof(C);
+  static constexpr size_t table_bytes = (size_t)NOPS * P * P * sizeof(C);  // as C^{(gamma,delta)}
   static constexpr size_t tile_bytes = (size_t)TS * sizeof(C);
   static int meta_bytes(int cap0, int cap1, int max_out) {
     // header, an item (8 bytes) per pass tile, one run (8 bytes) per output, padding
     const int items = cap1 + (D == 3 ? cap0 : 0) + max_out;
     return (kBlobHeader + 8 * items + 8 * max_out + 15) & ~15;
   }
-  // table | 4 mbarriers | 2 metadata slots | 2 input buffers | scratch (2 in 3D, where
-  // the last pass stages its outputs there)
+  // 4 mbarriers | 2 metadata slots | 2 input buffers | scratch (2 in 3D, where the last
+  // pass stages its outputs there)
   static constexpr int NSCR = D == 3 ? 2 : 1;
   static size_t bytes(const ChunkCaps &c) {
-    size_t b = (smem_table_bytes + 15) & ~(size_t)15;
-    b += 64;
+    size_t b = 64;
     b += 2 * (size_t)c.meta_bytes;
     return b + (2 * (size_t)c.cap0 + NSCR * (size_t)c.cap1) * tile_bytes;
   }
@@ -153,29 +145,67 @@ __device__ __forceinline__ bool consumer_any(bool v) {
   return r != 0;
 }
 
-// Accumulates y += T x for one fibre: x[l] = X[l * SK], T the operator at Tg (FP32:
-// transposed and padded, one 16-byte read gives T[m][l] and T[m+1][l]).
-template <typename R, int P, int PP, int SK>
-__device__ __forceinline__ void apply_op(const typename Cx<R>::T *Tg, const typename Cx<R>::T *X,
-                                         typename Cx<R>::T (&y)[P]) {
+// The factors of the transfer operators of this translation unit's p (BFLY_P), both
+// directions: c_w[adjoint][delta][m][l] (W(delta), or W(delta)^H) and
+// c_phi[adjoint][delta][l] (phi_1, or its conjugate).  The same for every plan of that p,
+// written once per device (init_operators).
+#ifndef BFLY_P
+#error "level.cuh is compiled once per p, with BFLY_P defined"
+#endif
+static __constant__ float2 c_w32[2][2][BFLY_P][BFLY_P];
+static __constant__ float2 c_phi32[2][2][BFLY_P];
+static __constant__ double2 c_w64[2][2][BFLY_P][BFLY_P];
+static __constant__ double2 c_phi64[2][2][BFLY_P];
+
+template <typename R, bool ADJ, int DL>
+__device__ __forceinline__ typename Cx<R>::T w_entry(int m, int l) {
+  if constexpr (sizeof(R) == 4)
+    return c_w32[ADJ][DL][m][l];
+  else
+    return c_w64[ADJ][DL][m][l];
+}
+template <typename R, bool ADJ, int DL>
+__device__ __forceinline__ typename Cx<R>::T phi_entry(int l) {
+  if constexpr (sizeof(R) == 4)
+    return c_phi32[ADJ][DL][l];
+  else
+    return c_phi64[ADJ][DL][l];
+}
+
+// y += C^{(gamma, DL)} x for one fibre, x_l = X[l * SK]: forward W(DL) (phi_gamma o x),
+// adjoint conj(phi_gamma) o (W(DL)^H x).  The loops are unrolled, so every entry of W and
+// phi has a compile-time address and is read as a constant-bank operand.
+template <typename R, int P, int SK, bool ADJ, int DL>
+__device__ __forceinline__ void apply_factored(bool gamma, const typename Cx<R>::T *X,
+                                               typename Cx<R>::T (&y)[P]) {
   using C = typename Cx<R>::T;
   C x[P];
 #pragma unroll
   for (int l = 0; l < P; ++l) x[l] = X[l * SK];
-  // l outer, m inner: P independent multiply-add chains in flight
+  if constexpr (!ADJ) {
+    if (gamma) {
 #pragma unroll
-  for (int l = 0; l < P; ++l) {
-    if constexpr (sizeof(R) == 4) {
-      const float4 *Tl = reinterpret_cast<const float4 *>(Tg + l * PP);
+      for (int l = 0; l < P; ++l) x[l] = cmul(phi_entry<R, ADJ, DL>(l), x[l]);
+    }
+    // l outer, m inner: P independent multiply-add chains in flight
 #pragma unroll
-      for (int m = 0; m < P; m += 2) {
-        const float4 t2 = Tl[m / 2];
-        y[m] = cfma(cmk((R)t2.x, (R)t2.y), x[l], y[m]);
-        if (m + 1 < P) y[m + 1] = cfma(cmk((R)t2.z, (R)t2.w), x[l], y[m + 1]);
-      }
+    for (int l = 0; l < P; ++l)
+#pragma unroll
+      for (int m = 0; m < P; ++m) y[m] = cfma(w_entry<R, ADJ, DL>(m, l), x[l], y[m]);
+  } else {
+    C v[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) v[m] = cmk((R)0, (R)0);
+#pragma unroll
+    for (int l = 0; l < P; ++l)
+#pragma unroll
+      for (int m = 0; m < P; ++m) v[m] = cfma(w_entry<R, ADJ, DL>(m, l), x[l], v[m]);
+    if (gamma) {
+#pragma unroll
+      for (int m = 0; m < P; ++m) y[m] = cfma(phi_entry<R, ADJ, DL>(m), v[m], y[m]);
     } else {
 #pragma unroll
-      for (int m = 0; m < P; ++m) y[m] = cfma(Tg[m * P + l], x[l], y[m]);
+      for (int m = 0; m < P; ++m) y[m] = cadd(y[m], v[m]);
     }
   }
 }
@@ -186,10 +216,10 @@ __device__ __forceinline__ void apply_op(const typename Cx<R>::T *Tg, const type
 // Each lane computes y = C^{op0} x0 (+ C^{op1} x1) along axis K for its fibre with its
 // item's operators and stores it to the item's destination tile (every destination of a
 // pass is written by exactly one item).
-template <typename R, int D, int P, int K>
+template <typename R, int D, int P, int K, bool ADJ>
 __device__ __forceinline__ void run_pass(const Item *items, int n_items, int n_two,
                                          const typename Cx<R>::T *src, typename Cx<R>::T *dst,
-                                         const typename Cx<R>::T *table, int warp, int lane) {
+                                         int warp, int lane) {
   using C = typename Cx<R>::T;
   using S = LevelShape<R, D, P>;
   constexpr int FIB = S::FIB, TS = S::TS;
@@ -212,24 +242,31 @@ __device__ __forceinline__ void run_pass(const Item *items, int n_items, int n_t
     C y[P];
 #pragma unroll
     for (int m = 0; m < P; ++m) y[m] = cmk((R)0, (R)0);
-    apply_op<R, P, S::PP, SK>(table + (size_t)(it.ops & 3) * S::OPS_S, src + (size_t)it.src0 * TS + base, y);
-    if (fl < nfib2)
-      apply_op<R, P, S::PP, SK>(table + (size_t)(it.ops >> 2) * S::OPS_S, src + (size_t)it.src1 * TS + base, y);
+    const int nsrc = fl < nfib2 ? 2 : 1;
+#pragma unroll 1
+    for (int j = 0; j < nsrc; ++j) {
+      const int op = j ? it.ops >> 2 : it.ops & 3;
+      const C *X = src + (size_t)(j ? it.src1 : it.src0) * TS + base;
+      if (op & 1)
+        apply_factored<R, P, SK, ADJ, 1>((op >> 1) != 0, X, y);
+      else
+        apply_factored<R, P, SK, ADJ, 0>((op >> 1) != 0, X, y);
+    }
     C *Y = dst + (size_t)it.dst * TS + base;
 #pragma unroll
     for (int m = 0; m < P; ++m) Y[m * SK] = y[m];
   }
 }
 
-template <typename R, int D, int P>
-__global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel(const LevelArgs a) {
+// FP64 blocks keep twice the registers (two blocks per SM): their operands are twice as wide.
+template <typename R, int D, int P, bool ADJ>
+__global__ void __launch_bounds__(kLevelThreads, sizeof(R) == 4 ? kLevelBlocksPerSm : kLevelBlocksPerSm / 2)
+    level_kernel(const LevelArgs a) {
   using C = typename Cx<R>::T;
   using S = LevelShape<R, D, P>;
-  constexpr int TS = S::TS, NOPS = S::NOPS;
+  constexpr int TS = S::TS;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char *ptr = smem;
-  C *s_table = reinterpret_cast<C *>(ptr);
-  ptr += (S::smem_table_bytes + 15) & ~(size_t)15;
   uint64_t *full = reinterpret_cast<uint64_t *>(ptr);  // full[2], staged[2]
   uint64_t *staged = full + 2;
   ptr += 64;
@@ -241,8 +278,6 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
   C *scr0 = slot0 + 2 * (size_t)a.cap0 * TS;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const C *table = reinterpret_cast<const C *>(a.table);
-  for (int e = tid; e < NOPS * S::OPS; e += kLevelThreads) s_table[(e / S::OPS) * S::OPS_S + e % S::OPS] = table[e];
   if (tid == 0) {
     mbar_init(&full[0], 1);
     mbar_init(&full[1], 1);
@@ -346,14 +381,14 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
     const int32_t *hdr = reinterpret_cast<const int32_t *>(meta_s);
     const Item *i0 = reinterpret_cast<const Item *>(meta_s + kBlobHeader);
     const Item *i1 = i0 + hdr[0];
-    run_pass<R, D, P, 0>(i0, hdr[0], hdr[3], in_s, scr, s_table, warp, lane);
+    run_pass<R, D, P, 0, ADJ>(i0, hdr[0], hdr[3], in_s, scr, warp, lane);
     consumer_sync();
     if (D == 3) {
-      run_pass<R, D, P, (D == 3 ? 1 : 0)>(i1, hdr[1], hdr[4], scr, in_s, s_table, warp, lane);
+      run_pass<R, D, P, (D == 3 ? 1 : 0), ADJ>(i1, hdr[1], hdr[4], scr, in_s, warp, lane);
       consumer_sync();
-      run_pass<R, D, P, D - 1>(i1 + hdr[1], hdr[2], hdr[5], in_s, scr, s_table, warp, lane);  // staged in scr
+      run_pass<R, D, P, D - 1, ADJ>(i1 + hdr[1], hdr[2], hdr[5], in_s, scr, warp, lane);  // staged in scr
     } else {
-      run_pass<R, D, P, D - 1>(i1, hdr[1], hdr[4], scr, in_s, s_table, warp, lane);  // staged in in_s
+      run_pass<R, D, P, D - 1, ADJ>(i1, hdr[1], hdr[4], scr, in_s, warp, lane);  // staged in in_s
     }
     fence_async_shared();  // the staged tiles are visible to the bulk stores
     consumer_sync();

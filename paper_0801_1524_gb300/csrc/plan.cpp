@@ -101,6 +101,27 @@ void leaf_weights(int p, double tau, double *w) {
   }
 }
 
+void transfer_factors(int p, bool adjoint, double *W, double *phi) {
+  // C^{(gamma,delta)} = W(delta) diag(phi_gamma), W(delta)_{ml} = w_m(tau_l),
+  // phi_0 = 1, phi_1[l] = e^{2 pi i tau_l} = e^{i pi (delta q + l)/q}; the adjoint
+  // operator is diag(conj phi_gamma) W(delta)^H.
+  const int q = p - 1;
+  std::vector<double> w((size_t)2 * p);
+  for (int delta = 0; delta < 2; ++delta)
+    for (int l = 0; l < p; ++l) {
+      const double tau = (double)(delta * q + l) / (2.0 * q);
+      leaf_weights(p, tau, w.data());
+      for (int m = 0; m < p; ++m) {
+        const size_t at = adjoint ? (((size_t)delta * p + l) * p + m) : (((size_t)delta * p + m) * p + l);
+        W[2 * at] = w[2 * m];
+        W[2 * at + 1] = adjoint ? -w[2 * m + 1] : w[2 * m + 1];
+      }
+      const double ang = M_PI * (double)(delta * q + l) / q;
+      phi[2 * (delta * p + l)] = std::cos(ang);
+      phi[2 * (delta * p + l) + 1] = adjoint ? -std::sin(ang) : std::sin(ang);
+    }
+}
+
 std::vector<double> transfer_table(int p, bool adjoint) {
   // Per axis, for A (index a, width w^A) and B (width w^B) with w^A w^B = N, the matching
   // condition of Sec. 2.1 with the evaluation of Fig. 1 gives f^{AB} = T f^{A'Bc},
@@ -242,8 +263,13 @@ StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp
           pass.push_back(e);
         }
       }
-      // two-source items first (a step then rarely mixes one- and two-source fibres)
-      std::stable_partition(pass.begin(), pass.end(), [](const Item &x) { return x.src1 != 0xffff; });
+      // two-source items first, then by the delta and gamma of the first operator: a
+      // step then rarely mixes one- and two-source fibres or operators of both deltas
+      std::stable_sort(pass.begin(), pass.end(), [](const Item &x, const Item &y) {
+        const int kx = ((x.src1 == 0xffff) << 2) | ((x.ops & 1) << 1) | ((x.ops >> 1) & 1);
+        const int ky = ((y.src1 == 0xffff) << 2) | ((y.ops & 1) << 1) | ((y.ops >> 1) & 1);
+        return kx < ky;
+      });
       icount[k] = (int32_t)pass.size();
       for (const Item &e : pass) tcount[k] += e.src1 != 0xffff;
       items.insert(items.end(), pass.begin(), pass.end());

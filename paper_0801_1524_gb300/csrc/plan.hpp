@@ -99,6 +99,12 @@ std::string build_tree(HostTree &T, int dim, int L, double N, double scale, int6
 // adjoint = true stores the conjugate transpose of every operator.
 std::vector<double> transfer_table(int p, bool adjoint);
 
+// The factors of the transfer operators, C^{(gamma,delta)} = W(delta) diag(phi_gamma)
+// (phi_0 = 1), as interleaved (re, im) doubles: W [2][p][p] (delta, row, column) and
+// phi [2][p] = phi_1 for delta = 0, 1.  adjoint = true gives the factors of the
+// conjugate-transposed operators, diag(conj phi_gamma) W(delta)^H: W^H and conj(phi_1).
+void transfer_factors(int p, bool adjoint, double *W /* 2*p*p*2 */, double *phi /* 2*p*2 */);
+
 // Lagrange weights of the leaf step, w_m(tau) = (G^{-1} v(tau))_m, m = 0..p-1, for
 // G_{ll'} = e^{2 pi i l l'/q^2}, v(tau)_l = e^{2 pi i l tau/q}, tau in leaf widths.
 void leaf_weights(int p, double tau, double *w /* 2p doubles */);

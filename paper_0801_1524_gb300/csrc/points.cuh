@@ -17,44 +17,49 @@
 namespace bfly {
 
 constexpr int kPointThreads = 256;
-constexpr int kSpreadBatch = 64;  // points staged in shared memory at a time
+constexpr int kSpreadPerThread = 4;  // tile elements per thread
 
 // tile[b][l] = sum_{j in leaf b} val_j prod_d W_j[d][l_d]   (conj(W) when a.conj)
-// One thread per tile element (b, l); a block covers 256 consecutive elements, i.e. a few
-// consecutive leaves, whose points are consecutive in sorted order.  The block stages
-// those points (value gathered through perm, weight rows) in shared memory, 64 at a time,
-// so that every point is read from memory once and the loads of a batch are in flight
-// together; then each thread sums its leaf's points of the batch.
+// A block covers 1024 consecutive tile elements (b, l) (four per thread, 256 apart so that
+// the stores are coalesced), i.e. the consecutive leaves of those elements, whose points
+// are consecutive in sorted order.  The block stages those points (value gathered through
+// perm, weight rows) in shared memory, a batch at a time, so that every point is read
+// from memory once and the loads of a batch are in flight together; then each thread sums
+// the batch's points of its elements' leaves.
 template <typename R, int D, int P>
 __global__ void __launch_bounds__(kPointThreads) spread_kernel(const PointArgs a) {
   using C = typename Cx<R>::T;
-  constexpr int PD = ipow(P, D);
-  __shared__ C s_v[kSpreadBatch];
-  __shared__ C s_w[kSpreadBatch][D * P];
+  constexpr int PD = ipow(P, D), E = kPointThreads * kSpreadPerThread;
+  constexpr int BATCH = (24576 / ((D * P + 1) * (int)sizeof(C))) / 32 * 32;
+  __shared__ C s_v[BATCH];
+  __shared__ C s_w[BATCH][D * P];
   const int64_t n_el = a.nbox * PD;
-  const int64_t e0 = (int64_t)blockIdx.x * kPointThreads;
-  const int64_t w = e0 + threadIdx.x;
+  const int64_t e0 = (int64_t)blockIdx.x * E;
   const int r = blockIdx.y;
-  const bool active = w < n_el;
-  const int64_t b = active ? w / PD : 0;
-  const int l = active ? (int)(w - b * PD) : 0;
-  int ld[D];
-  {
-    int rem = l;
+  int64_t bk[kSpreadPerThread];
+  int lk[kSpreadPerThread][D], j0[kSpreadPerThread], j1[kSpreadPerThread];
+  C acc[kSpreadPerThread];
+#pragma unroll
+  for (int k = 0; k < kSpreadPerThread; ++k) {
+    const int64_t w = e0 + threadIdx.x + k * kPointThreads;
+    const bool on = w < n_el;
+    bk[k] = on ? w / PD : -1;
+    int rem = on ? (int)(w - bk[k] * PD) : 0;
 #pragma unroll
     for (int d = D - 1; d >= 0; --d) {
-      ld[d] = rem % P;
+      lk[k][d] = rem % P;
       rem /= P;
     }
+    j0[k] = on ? a.leaf_start[bk[k]] : 0;
+    j1[k] = on ? a.leaf_start[bk[k] + 1] : 0;
+    acc[k] = cmk((R)0, (R)0);
   }
   // the block's points: those of leaves e0/PD .. (last element)/PD
-  const int64_t e1 = min(n_el, e0 + kPointThreads);
+  const int64_t e1 = min(n_el, e0 + E);
   const int jb0 = a.leaf_start[e0 / PD], jb1 = a.leaf_start[(e1 - 1) / PD + 1];
-  const int j0 = active ? a.leaf_start[b] : 0, j1 = active ? a.leaf_start[b + 1] : 0;
   const C *W = reinterpret_cast<const C *>(a.W);
-  C acc = cmk((R)0, (R)0);
-  for (int pb = jb0; pb < jb1; pb += kSpreadBatch) {
-    const int n = min(kSpreadBatch, jb1 - pb);
+  for (int pb = jb0; pb < jb1; pb += BATCH) {
+    const int n = min(BATCH, jb1 - pb);
     for (int t = threadIdx.x; t < n; t += kPointThreads)
       s_v[t] = load_io<C>(a.vin, (int64_t)r * a.n_total + a.perm[pb + t], a.io64);
     for (int t = threadIdx.x; t < n * D * P; t += kPointThreads) {
@@ -62,16 +67,24 @@ __global__ void __launch_bounds__(kPointThreads) spread_kernel(const PointArgs a
       s_w[t / (D * P)][t % (D * P)] = a.conj ? cconj(wv) : wv;
     }
     __syncthreads();
-    const int ja = max(j0, pb) - pb, jz = min(j1, pb + n) - pb;
-    for (int j = ja; j < jz; ++j) {
-      C wt = s_w[j][ld[0]];
 #pragma unroll
-      for (int d = 1; d < D; ++d) wt = cmul(wt, s_w[j][d * P + ld[d]]);
-      acc = cfma(wt, s_v[j], acc);
+    for (int k = 0; k < kSpreadPerThread; ++k) {
+      const int ja = max(j0[k], pb) - pb, jz = min(j1[k], pb + n) - pb;
+      for (int j = ja; j < jz; ++j) {
+        C wt = s_w[j][lk[k][0]];
+#pragma unroll
+        for (int d = 1; d < D; ++d) wt = cmul(wt, s_w[j][d * P + lk[k][d]]);
+        acc[k] = cfma(wt, s_v[j], acc[k]);
+      }
     }
     __syncthreads();
   }
-  if (active) reinterpret_cast<C *>(a.vout)[(size_t)r * a.tile_rhs + (size_t)b * a.tile_stride + l] = acc;
+#pragma unroll
+  for (int k = 0; k < kSpreadPerThread; ++k)
+    if (bk[k] >= 0) {
+      const int l = (int)(e0 + threadIdx.x + k * kPointThreads - bk[k] * PD);
+      reinterpret_cast<C *>(a.vout)[(size_t)r * a.tile_rhs + (size_t)bk[k] * a.tile_stride + l] = acc[k];
+    }
 }
 
 constexpr int kInterpLanes = 8;  // lanes per target
