@@ -257,6 +257,20 @@ def main_bfly(args, rank, world, dist):
         e2e.append(time.perf_counter() - t0)
     e2e_s = float(np.mean(e2e))
 
+    # ---- the adjoint sweep (the gradient's transform) on the same plan, device buffers
+    v_adj = torch.empty(nk, dtype=torch.complex64, device=dev)
+    for _ in range(3):
+        plan.adjoint(u, out=v_adj)
+    adj_ms = []
+    for _ in range(max(10, min(args.steps, 100))):
+        flush_l2(flush)
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_ev.record(stream)
+        plan.adjoint(u, out=v_adj)
+        b_ev.record(stream)
+        b_ev.synchronize()
+        adj_ms.append(a_ev.elapsed_time(b_ev))
+
     if rank != 0:
         return None
 
@@ -354,6 +368,8 @@ def main_bfly(args, rank, world, dist):
                 "d2h_bytes_per_step": nx * 8, "ms": e2e_s * 1e3,
                 "call": "bfly_execute_host (pinned host buffers)"},
         "roofline": main,
+        "adjoint": {"ms": float(np.mean(adj_ms)), "transforms_per_s": 1e3 / float(np.mean(adj_ms)),
+                    "call": "bfly_execute_adjoint (device buffers; the sweep behind the gradient)"},
         "gpu_launches": args.steps * (L + 2),
         "clocks": clk,
         "plan": {"seconds": info["plan_seconds"], "L": L, "total_pairs": info["total_pairs"],
