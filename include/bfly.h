@@ -106,7 +106,8 @@ typedef struct {
  *   out      receives the plan; *out is NULL on failure.
  *   dim      2 or 3.   N: finite, > 0.   p: 3, 5, 7 or 9.
  *   x, k     host arrays [nx][dim] and [nk][dim], every coordinate finite and in [0,N];
- *            copied, the caller keeps ownership.  nx, nk >= 1.
+ *            copied, the caller keeps ownership.  nx, nk >= 0 (x or k may be NULL when
+ *            its count is 0: the transform then returns zeros, or nothing).
  *   opts     NULL for defaults.
  * Errors: INVALID_ARG (any of the above), UNSUPPORTED (even p; N beyond 2^30 in 2D or
  * 2^20 in 3D; a p or precision whose workspace does not fit on chip), OUT_OF_MEMORY,
@@ -126,7 +127,8 @@ void bfly_plan_destroy(bfly_plan_t plan);
  * the recursive step for t = L-1 .. 0, and evaluation at the targets.
  *   f   device [nrhs][nk] sources (dtype), read only.
  *   u   device [nrhs][nx] potentials (dtype), overwritten.
- *   1 <= nrhs <= max_nrhs of the plan.  f and u must not overlap.
+ *   1 <= nrhs <= max_nrhs of the plan.  f and u must not overlap.  A pointer may be NULL
+ *   when its side has no points; with no sources u is set to zero.
  * The arithmetic is the plan's precision whatever the I/O dtype.
  */
 bfly_status bfly_execute(bfly_plan_t plan, const void *f, void *u, int nrhs, int dtype,

@@ -124,9 +124,9 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   const int L = levels_for(N);
   if ((dim == 2 && L > 30) || (dim == 3 && L > 20))
     return fail(BFLY_ERR_UNSUPPORTED, "N too large for 64-bit Morton keys");
-  if (nx < 1 || nk < 1 || nx > INT32_MAX / 2 || nk > INT32_MAX / 2)
-    return fail(BFLY_ERR_INVALID_ARG, "nx and nk must be in [1, 2^30)");
-  if (!x || !k) return fail(BFLY_ERR_INVALID_ARG, "x or k is NULL");
+  if (nx < 0 || nk < 0 || nx > INT32_MAX / 2 || nk > INT32_MAX / 2)
+    return fail(BFLY_ERR_INVALID_ARG, "nx and nk must be in [0, 2^30)");
+  if ((nx > 0 && !x) || (nk > 0 && !k)) return fail(BFLY_ERR_INVALID_ARG, "x or k is NULL");
   bfly_opts o{};
   o.prec = BFLY_PREC_FP32;
   o.max_nrhs = 1;
@@ -387,10 +387,12 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
 
 namespace {
 
-bfly_status check_exec(bfly_plan_t P, const void *a, const void *b, int nrhs, int dtype) {
+bfly_status check_exec(bfly_plan_t P, const void *a, const void *b, int nrhs, int dtype, bool adjoint) {
   if (!P) return fail(BFLY_ERR_INVALID_ARG, "plan is NULL");
   if (!P->dmem) return fail(BFLY_ERR_INVALID_ARG, "plan was created host-only");
-  if (!a || !b) return fail(BFLY_ERR_INVALID_ARG, "data pointer is NULL");
+  // a pointer may be NULL only when its side has no points
+  const int64_t n_a = adjoint ? P->nx : P->nk, n_b = adjoint ? P->nk : P->nx;
+  if ((!a && n_a > 0) || (!b && n_b > 0)) return fail(BFLY_ERR_INVALID_ARG, "data pointer is NULL");
   if (nrhs < 1 || nrhs > P->max_nrhs) return fail(BFLY_ERR_INVALID_ARG, "nrhs outside 1..max_nrhs");
   if (dtype != BFLY_C64 && dtype != BFLY_C128) return fail(BFLY_ERR_INVALID_ARG, "unknown dtype");
   return BFLY_OK;
@@ -407,6 +409,14 @@ bfly_status run(bfly_plan_t P, const void *in, void *out, int nrhs, int dtype, b
     cudaEvent_t e = ev ? ev[n++] : nullptr;
     return e ? cudaEventRecord(e, s) : cudaSuccess;
   };
+  // an empty side: nothing to compute (no outputs) or every output is zero (no inputs)
+  const int64_t n_in = adjoint ? P->nx : P->nk, n_out = adjoint ? P->nk : P->nx;
+  if (n_in == 0 || n_out == 0) {
+    BFLY_CUDA(mark());
+    if (n_out > 0) BFLY_CUDA(cudaMemsetAsync(out, 0, (size_t)nrhs * n_out * (io64 ? 16 : 8), s));
+    while (ev && n < L + 3) BFLY_CUDA(mark());
+    return BFLY_OK;
+  }
   if (!adjoint) {
     // step 2: leaf charges (stage L) from the sources
     BFLY_CUDA(mark());
@@ -441,7 +451,7 @@ extern "C" {
 
 bfly_status bfly_execute(bfly_plan_t plan, const void *f, void *u, int nrhs, int dtype, void *stream) {
   g_err.clear();
-  bfly_status st = check_exec(plan, f, u, nrhs, dtype);
+  bfly_status st = check_exec(plan, f, u, nrhs, dtype, false);
   if (st != BFLY_OK) return st;
   return run(plan, f, u, nrhs, dtype, false, reinterpret_cast<cudaStream_t>(stream));
 }
@@ -449,7 +459,7 @@ bfly_status bfly_execute(bfly_plan_t plan, const void *f, void *u, int nrhs, int
 bfly_status bfly_execute_adjoint(bfly_plan_t plan, const void *u, void *f, int nrhs, int dtype,
                                  void *stream) {
   g_err.clear();
-  bfly_status st = check_exec(plan, u, f, nrhs, dtype);
+  bfly_status st = check_exec(plan, u, f, nrhs, dtype, true);
   if (st != BFLY_OK) return st;
   return run(plan, u, f, nrhs, dtype, true, reinterpret_cast<cudaStream_t>(stream));
 }
@@ -457,15 +467,17 @@ bfly_status bfly_execute_adjoint(bfly_plan_t plan, const void *u, void *f, int n
 bfly_status bfly_execute_host(bfly_plan_t plan, const void *in_host, void *out_host, int nrhs,
                               int dtype, int adjoint, void *stream) {
   g_err.clear();
-  bfly_status st = check_exec(plan, in_host, out_host, nrhs, dtype);
+  bfly_status st = check_exec(plan, in_host, out_host, nrhs, dtype, adjoint != 0);
   if (st != BFLY_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t eb = dtype == BFLY_C128 ? 16 : 8;
   const int64_t nin = adjoint ? plan->nx : plan->nk, nout = adjoint ? plan->nk : plan->nx;
-  BFLY_CUDA(cudaMemcpyAsync(plan->stage_in, in_host, (size_t)nin * nrhs * eb, cudaMemcpyHostToDevice, s));
+  if (nin > 0)
+    BFLY_CUDA(cudaMemcpyAsync(plan->stage_in, in_host, (size_t)nin * nrhs * eb, cudaMemcpyHostToDevice, s));
   st = run(plan, plan->stage_in, plan->stage_out, nrhs, dtype, adjoint != 0, s);
   if (st != BFLY_OK) return st;
-  BFLY_CUDA(cudaMemcpyAsync(out_host, plan->stage_out, (size_t)nout * nrhs * eb, cudaMemcpyDeviceToHost, s));
+  if (nout > 0)
+    BFLY_CUDA(cudaMemcpyAsync(out_host, plan->stage_out, (size_t)nout * nrhs * eb, cudaMemcpyDeviceToHost, s));
   BFLY_CUDA(cudaStreamSynchronize(s));
   return BFLY_OK;
 }
@@ -473,7 +485,7 @@ bfly_status bfly_execute_host(bfly_plan_t plan, const void *in_host, void *out_h
 bfly_status bfly_execute_events(bfly_plan_t plan, const void *in, void *out, int nrhs, int dtype,
                                 int adjoint, void *stream, void *const *events, int n_events) {
   g_err.clear();
-  bfly_status st = check_exec(plan, in, out, nrhs, dtype);
+  bfly_status st = check_exec(plan, in, out, nrhs, dtype, adjoint != 0);
   if (st != BFLY_OK) return st;
   if (!events || n_events != plan->L + 3) return fail(BFLY_ERR_INVALID_ARG, "events must hold L + 3 entries");
   return run(plan, in, out, nrhs, dtype, adjoint != 0, reinterpret_cast<cudaStream_t>(stream),
@@ -483,7 +495,7 @@ bfly_status bfly_execute_events(bfly_plan_t plan, const void *in, void *out, int
 bfly_status bfly_direct(bfly_plan_t plan, const void *in, void *out, int nrhs, int dtype, int adjoint,
                         void *stream) {
   g_err.clear();
-  bfly_status st = check_exec(plan, in, out, nrhs, dtype);
+  bfly_status st = check_exec(plan, in, out, nrhs, dtype, adjoint != 0);
   if (st != BFLY_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int prec = plan->prec == BFLY_PREC_FP64 ? 0 : 1;

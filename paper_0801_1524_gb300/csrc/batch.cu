@@ -45,8 +45,13 @@ using bfly_state::set_error;
 bfly_status launch_all(bfly_batch_t B, const void *const *f, void *const *u, int nrhs, int dtype,
                        cudaStream_t s) {
   const bool io64 = dtype == BFLY_C128;
+  auto empty = [](bfly_plan_t P) { return P->nx == 0 || P->nk == 0; };
   for (int i = 0; i < B->count; ++i) {
     bfly_plan_t P = B->plans[i];
+    if (empty(P)) {  // no targets: nothing; no sources: zero potentials
+      if (P->nx > 0) BATCH_CUDA(cudaMemsetAsync(u[i], 0, (size_t)nrhs * P->nx * (io64 ? 16 : 8), s));
+      continue;
+    }
     BATCH_CUDA(P->ks->spread(point_args(P, false, f[i], P->buf[P->L & 1], nrhs, io64, false,
                                         P->pairs[P->L] * P->TS), s));
   }
@@ -68,6 +73,7 @@ bfly_status launch_all(bfly_batch_t B, const void *const *f, void *const *u, int
   }
   for (int i = 0; i < B->count; ++i) {
     bfly_plan_t P = B->plans[i];
+    if (empty(P)) continue;
     BATCH_CUDA(P->ks->interp(point_args(P, true, P->buf[0], u[i], nrhs, io64, false,
                                         P->pairs[0] * P->TS), s));
   }
@@ -179,7 +185,8 @@ bfly_status bfly_batch_execute(bfly_batch_t B, const void *const *f, void *const
   if (nrhs < 1 || nrhs > B->max_nrhs) return set_error(BFLY_ERR_INVALID_ARG, "nrhs outside 1..max_nrhs of the plans");
   if (dtype != BFLY_C64 && dtype != BFLY_C128) return set_error(BFLY_ERR_INVALID_ARG, "unknown dtype");
   for (int i = 0; i < B->count; ++i)
-    if (!f[i] || !u[i]) return set_error(BFLY_ERR_INVALID_ARG, "a data pointer is NULL");
+    if ((!f[i] && B->plans[i]->nk > 0) || (!u[i] && B->plans[i]->nx > 0))
+      return set_error(BFLY_ERR_INVALID_ARG, "a data pointer is NULL");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!s) return launch_all(B, f, u, nrhs, dtype, s);  // the legacy stream cannot be captured
   const bool same = B->exec && B->key_nrhs == nrhs && B->key_dtype == dtype && B->key_stream == s &&

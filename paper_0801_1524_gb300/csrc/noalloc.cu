@@ -64,7 +64,8 @@ extern "C" bfly_status bfly_execute_noalloc(bfly_plan_t plan, const void *f, voi
   bfly_state::set_error(BFLY_OK, "");
   if (!plan) return bfly_state::set_error(BFLY_ERR_INVALID_ARG, "plan is NULL");
   if (!plan->dmem) return bfly_state::set_error(BFLY_ERR_INVALID_ARG, "plan was created host-only");
-  if (!f || !u) return bfly_state::set_error(BFLY_ERR_INVALID_ARG, "data pointer is NULL");
+  if ((!f && plan->nk > 0) || (!u && plan->nx > 0))
+    return bfly_state::set_error(BFLY_ERR_INVALID_ARG, "data pointer is NULL");
   if (nrhs < 1 || nrhs > plan->max_nrhs)
     return bfly_state::set_error(BFLY_ERR_INVALID_ARG, "nrhs outside 1..max_nrhs");
   if (dtype != BFLY_C64 && dtype != BFLY_C128) return bfly_state::set_error(BFLY_ERR_INVALID_ARG, "unknown dtype");
@@ -86,6 +87,11 @@ extern "C" bfly_status bfly_execute_noalloc(bfly_plan_t plan, const void *f, voi
   // the forward sweep of bfly_execute, on the static buffers
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const bool io64 = dtype == BFLY_C128;
+  if (plan->nx == 0) return BFLY_OK;  // no targets
+  if (plan->nk == 0) {                // no sources: every potential is zero
+    NOALLOC_CUDA(cudaMemsetAsync(u, 0, (size_t)nrhs * plan->nx * (io64 ? 16 : 8), s));
+    return BFLY_OK;
+  }
   const int L = plan->L, TS = plan->TS;
   NOALLOC_CUDA(plan->ks->spread(point_args(plan, false, f, buf[L & 1], nrhs, io64, false,
                                            plan->pairs[L] * TS), s));

@@ -121,7 +121,7 @@ class Plan:
         if not isinstance(t, torch.Tensor) or not t.is_cuda:
             raise TypeError(f"{name} must be a CUDA tensor")
         squeeze = t.dim() == 1
-        t2 = t.reshape(1, -1) if squeeze else t
+        t2 = t.reshape(1, t.shape[0]) if squeeze else t
         if t2.dim() != 2 or t2.shape[1] != n:
             raise ValueError(f"{name} must be [{n}] or [nrhs, {n}]")
         return t2.contiguous(), squeeze
@@ -209,7 +209,10 @@ class Batch:
     def forward(self, fs, us=None, stream=None):
         """fs: list of [nrhs, nk_i] CUDA tensors (same dtype); returns / fills us."""
         torch = _torch()
-        fs = [f.reshape(-1, p.nk).contiguous() for f, p in zip(fs, self.plans)]
+        fs = [(f if f.dim() == 2 else f.reshape(1, f.shape[0])).contiguous() for f in fs]
+        for f, p in zip(fs, self.plans):
+            if f.shape[1] != p.nk:
+                raise ValueError(f"batch input must be [nrhs, {p.nk}]")
         nrhs = fs[0].shape[0]
         if us is None:
             us = [torch.empty((nrhs, p.nx), dtype=fs[0].dtype, device=fs[0].device) for p in self.plans]

@@ -99,3 +99,22 @@ def test_curve_workload_plan_counts():
     assert all(a * b <= 12 * inst.N for _, a, b in st)
     assert info["tiles_written_fwd"] == sum(a * b for t, a, b in st if t < 13)
     assert info["plan_seconds"] < 5.0
+
+
+@pytest.mark.parametrize("nx,nk", [(0, 40), (40, 0), (0, 0)])
+def test_empty_sides_are_accepted(nx, nk):
+    x = w.random_points(nx, 64.0, 2, 1)
+    k = w.random_points(nk, 64.0, 2, 2)
+    P = Plan(x, k, 64.0, 5, host_only=True)
+    info = P.info()
+    assert (info["nx"], info["nk"]) == (nx, nk)
+    # no non-empty box on an empty side: every stage pairs zero boxes with the other tree
+    assert info["total_pairs"] == 0 and info["chunks_fwd"] == 0
+    lib = native.load()
+    h = ctypes.c_void_p()
+    o = native.Opts()
+    o.prec, o.max_nrhs, o.flags = 1, 1, native.BFLY_FLAG_HOST_ONLY
+    assert lib.bfly_plan_create(ctypes.byref(h), 2, 64.0, nx, None, nk, None if nk == 0 else
+                                np.ascontiguousarray(k).ctypes.data, 5, ctypes.byref(o)) == (1 if nx > 0 else 0)
+    if h.value:
+        lib.bfly_plan_destroy(h)

@@ -174,3 +174,32 @@ def test_execute_host_matches_device():
     assert np.array_equal(dev, host)
     ua = P.execute_host(host, adjoint=True)
     assert np.array_equal(ua, P.adjoint(_gpu(host, torch.complex64)).cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_empty_sides(prec):
+    # no sources: every potential is zero; no targets: an empty result; the adjoint mirrors
+    from paper_0801_1524_gb300.plan import Batch, Plan
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    x = w.random_points(50, 64.0, 2, 1)
+    none = np.zeros((0, 2))
+    P = Plan(x, none, 64.0, 5, precision=prec, max_nrhs=2)
+    u = P.forward(torch.zeros((2, 0), dtype=dt, device="cuda"), out=torch.full((2, 50), 7.0, dtype=dt, device="cuda"))
+    assert u.shape == (2, 50) and torch.count_nonzero(u).item() == 0
+    assert P.adjoint(torch.ones((2, 50), dtype=dt, device="cuda")).shape == (2, 0)
+    uh = P.execute_host(np.zeros((1, 0), dtype=np.complex128))
+    assert uh.shape == (1, 50) and not np.any(uh)
+    Q = Plan(none, x, 64.0, 5, precision=prec)
+    assert Q.forward(torch.ones(50, dtype=dt, device="cuda")).shape == (0,)
+    g = Q.adjoint(torch.zeros(0, dtype=dt, device="cuda"))
+    assert g.shape == (50,) and torch.count_nonzero(g).item() == 0
+    torch.cuda.synchronize()
+    # a batch with an empty member next to a regular one
+    inst = w.small_random(2, 64.0, 5, 300, 200, 3)
+    R = Plan(inst.x, inst.k, 64.0, 5, precision=prec)
+    f = torch.as_tensor(inst.sources()[0], device="cuda").to(dt)
+    B = Batch([P, R])
+    us = B.forward([torch.zeros((1, 0), dtype=dt, device="cuda"), f.reshape(1, -1)])
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(us[0]).item() == 0
+    assert torch.equal(us[1].reshape(-1), R.forward(f))
