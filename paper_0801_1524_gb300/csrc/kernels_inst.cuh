@@ -29,7 +29,11 @@ cudaError_t init_operators() {
   if (ready) return cudaSuccess;
   constexpr int P = BFLY_P;
   std::vector<C> w((size_t)2 * 2 * P * P), phi((size_t)2 * 2 * P);
+  std::vector<float4> wp(w.size()), phip(phi.size());  // FP32: packed (re, re, -im, im)
   std::vector<double> wd((size_t)2 * P * P * 2), pd((size_t)2 * P * 2);
+  auto pack = [](double re, double im) {
+    return make_float4((float)re, (float)re, -(float)im, (float)im);
+  };
   for (int adj = 0; adj < 2; ++adj) {
     transfer_factors(P, adj != 0, wd.data(), pd.data());
     for (int i = 0; i < 2 * P * P; ++i) {
@@ -37,17 +41,19 @@ cudaError_t init_operators() {
       c.x = (R)wd[2 * i];
       c.y = (R)wd[2 * i + 1];
       w[(size_t)adj * 2 * P * P + i] = c;
+      wp[(size_t)adj * 2 * P * P + i] = pack(wd[2 * i], wd[2 * i + 1]);
     }
     for (int i = 0; i < 2 * P; ++i) {
       C c;
       c.x = (R)pd[2 * i];
       c.y = (R)pd[2 * i + 1];
       phi[(size_t)adj * 2 * P + i] = c;
+      phip[(size_t)adj * 2 * P + i] = pack(pd[2 * i], pd[2 * i + 1]);
     }
   }
   if constexpr (sizeof(R) == 4) {
-    e = cudaMemcpyToSymbol(c_w32, w.data(), w.size() * sizeof(C));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_phi32, phi.data(), phi.size() * sizeof(C));
+    e = cudaMemcpyToSymbol(c_w32, wp.data(), wp.size() * sizeof(float4));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_phi32, phip.data(), phip.size() * sizeof(float4));
   } else {
     e = cudaMemcpyToSymbol(c_w64, w.data(), w.size() * sizeof(C));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_phi64, phi.data(), phi.size() * sizeof(C));

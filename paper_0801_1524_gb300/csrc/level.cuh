@@ -23,7 +23,7 @@
 // every lane of a step computes y = C^{op0} x0 (+ C^{op1} x1) for its fibre.  Each
 // operator is applied in its factored form C^{(gamma,delta)} = W(delta) diag(phi_gamma):
 // the lane's own diagonal (phi_0 = 1), then W(delta), whose entries live in constant
-// memory and enter the multiply-adds as constant-bank operands (delta is the same in
+// memory and enter the (paired, f32x2) multiply-adds as warp-uniform operands (delta is the same in
 // every lane of a step but at most one step per pass, where the two halves run one after
 // the other).  Per fibre: P (or 2P) shared-memory loads, P^2 (or 2P^2) complex
 // multiply-adds, P stores; one barrier per pass.  The last
@@ -152,29 +152,43 @@ __device__ __forceinline__ bool consumer_any(bool v) {
 #ifndef BFLY_P
 #error "level.cuh is compiled once per p, with BFLY_P defined"
 #endif
-static __constant__ float2 c_w32[2][2][BFLY_P][BFLY_P];
-static __constant__ float2 c_phi32[2][2][BFLY_P];
+// FP32 entries are stored packed as (re, re, -im, im): a complex multiply-add is then two
+// paired multiply-adds (fma.rn.f32x2), (re, re) * (x.x, x.y) + (-im, im) * (x.y, x.x),
+// with the same roundings and order as the four scalar ones.
+static __constant__ float4 c_w32[2][2][BFLY_P][BFLY_P];
+static __constant__ float4 c_phi32[2][2][BFLY_P];
 static __constant__ double2 c_w64[2][2][BFLY_P][BFLY_P];
 static __constant__ double2 c_phi64[2][2][BFLY_P];
 
-template <typename R, bool ADJ, int DL>
-__device__ __forceinline__ typename Cx<R>::T w_entry(int m, int l) {
-  if constexpr (sizeof(R) == 4)
-    return c_w32[ADJ][DL][m][l];
-  else
-    return c_w64[ADJ][DL][m][l];
+template <bool ADJ, int DL>
+__device__ __forceinline__ float4 w_packed(int m, int l) { return c_w32[ADJ][DL][m][l]; }
+template <bool ADJ, int DL>
+__device__ __forceinline__ float4 phi_packed(int l) { return c_phi32[ADJ][DL][l]; }
+template <bool ADJ, int DL>
+__device__ __forceinline__ double2 w_entry64(int m, int l) { return c_w64[ADJ][DL][m][l]; }
+template <bool ADJ, int DL>
+__device__ __forceinline__ double2 phi_entry64(int l) { return c_phi64[ADJ][DL][l]; }
+
+// acc + c x for a packed constant c = (re, re, -im, im)
+__device__ __forceinline__ float2 cmac2(float4 c, float2 x, float2 acc) {
+  acc = __ffma2_rn(make_float2(c.x, c.y), x, acc);
+  return __ffma2_rn(make_float2(c.z, c.w), make_float2(x.y, x.x), acc);
 }
-template <typename R, bool ADJ, int DL>
-__device__ __forceinline__ typename Cx<R>::T phi_entry(int l) {
-  if constexpr (sizeof(R) == 4)
-    return c_phi32[ADJ][DL][l];
-  else
-    return c_phi64[ADJ][DL][l];
+__device__ __forceinline__ float2 cmul2(float4 c, float2 x) {
+  return cmac2(c, x, make_float2(0.0f, 0.0f));
 }
 
 // y += C^{(gamma, DL)} x for one fibre, x_l = X[l * SK]: forward W(DL) (phi_gamma o x),
 // adjoint conj(phi_gamma) o (W(DL)^H x).  The loops are unrolled, so every entry of W and
 // phi has a compile-time address and is read as a constant-bank operand.
+// One source of a lane's fibre, x = X[l * SK]:
+//   forward  y += W(DL) (phi_gamma o x)
+//   adjoint  y += W(DL)^H x, then, for gamma = 1, y = conj(phi_1) o y (the caller takes
+//            the gamma = 1 source of an item first, so that the scaling applies to that
+//            source alone and no second accumulator is needed).
+// The loops are unrolled: every entry of W and phi has a compile-time address in constant
+// memory.  (Two fibres per lane sharing each entry measured 15-29 % slower: larger
+// unrolled bodies and register pressure.)
 template <typename R, int P, int SK, bool ADJ, int DL>
 __device__ __forceinline__ void apply_factored(bool gamma, const typename Cx<R>::T *X,
                                                typename Cx<R>::T (&y)[P]) {
@@ -182,30 +196,32 @@ __device__ __forceinline__ void apply_factored(bool gamma, const typename Cx<R>:
   C x[P];
 #pragma unroll
   for (int l = 0; l < P; ++l) x[l] = X[l * SK];
-  if constexpr (!ADJ) {
-    if (gamma) {
+  if constexpr (sizeof(R) == 4) {
+    if (!ADJ && gamma) {
 #pragma unroll
-      for (int l = 0; l < P; ++l) x[l] = cmul(phi_entry<R, ADJ, DL>(l), x[l]);
+      for (int l = 0; l < P; ++l) x[l] = cmul2(phi_packed<ADJ, DL>(l), x[l]);
     }
     // l outer, m inner: P independent multiply-add chains in flight
 #pragma unroll
     for (int l = 0; l < P; ++l)
 #pragma unroll
-      for (int m = 0; m < P; ++m) y[m] = cfma(w_entry<R, ADJ, DL>(m, l), x[l], y[m]);
-  } else {
-    C v[P];
+      for (int m = 0; m < P; ++m) y[m] = cmac2(w_packed<ADJ, DL>(m, l), x[l], y[m]);
+    if (ADJ && gamma) {
 #pragma unroll
-    for (int m = 0; m < P; ++m) v[m] = cmk((R)0, (R)0);
+      for (int m = 0; m < P; ++m) y[m] = cmul2(phi_packed<ADJ, DL>(m), y[m]);
+    }
+  } else {
+    if (!ADJ && gamma) {
+#pragma unroll
+      for (int l = 0; l < P; ++l) x[l] = cmul(phi_entry64<ADJ, DL>(l), x[l]);
+    }
 #pragma unroll
     for (int l = 0; l < P; ++l)
 #pragma unroll
-      for (int m = 0; m < P; ++m) v[m] = cfma(w_entry<R, ADJ, DL>(m, l), x[l], v[m]);
-    if (gamma) {
+      for (int m = 0; m < P; ++m) y[m] = cfma(w_entry64<ADJ, DL>(m, l), x[l], y[m]);
+    if (ADJ && gamma) {
 #pragma unroll
-      for (int m = 0; m < P; ++m) y[m] = cfma(phi_entry<R, ADJ, DL>(m), v[m], y[m]);
-    } else {
-#pragma unroll
-      for (int m = 0; m < P; ++m) y[m] = cadd(y[m], v[m]);
+      for (int m = 0; m < P; ++m) y[m] = cmul(phi_entry64<ADJ, DL>(m), y[m]);
     }
   }
 }
@@ -244,7 +260,8 @@ __device__ __forceinline__ void run_pass(const Item *items, int n_items, int n_t
     for (int m = 0; m < P; ++m) y[m] = cmk((R)0, (R)0);
     const int nsrc = fl < nfib2 ? 2 : 1;
 #pragma unroll 1
-    for (int j = 0; j < nsrc; ++j) {
+    for (int jj = 0; jj < nsrc; ++jj) {
+      const int j = (ADJ && nsrc == 2) ? 1 - jj : jj;  // adjoint: the gamma = 1 source first
       const int op = j ? it.ops >> 2 : it.ops & 3;
       const C *X = src + (size_t)(j ? it.src1 : it.src0) * TS + base;
       if (op & 1)
