@@ -65,7 +65,8 @@ typedef struct {
   int prec;                /* bfly_precision; default BFLY_PREC_FP32 */
   int max_nrhs;            /* workspace is sized for up to this many right-hand sides (>= 1) */
   unsigned flags;          /* BFLY_FLAG_* */
-  int smem_kb;             /* shared memory per block for the recursive step, 0 = default */
+  int smem_kb;             /* shared memory per block for the recursive step, 0 = default
+                              (55 KB in 2D, 73 KB in 3D) */
   const char *tune_cache;  /* autotuning cache file (text), or NULL */
   int reserved[2];         /* must be zero */
 } bfly_opts;

@@ -208,7 +208,9 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   }
   P->TS = P->ks->tile_stride;
   // capacities: the largest chunk that fits the shared-memory budget of one block
-  const size_t want = (size_t)(o.smem_kb > 0 ? o.smem_kb : 55) * 1024;
+  // default budget: four blocks per SM in 2D; in 3D (8x larger tiles at p = 5) fewer,
+  // larger blocks, whose chunks hold enough tiles to keep the consumer warps busy
+  const size_t want = (size_t)(o.smem_kb > 0 ? o.smem_kb : (dim == 3 ? 73 : 55)) * 1024;
   auto caps_for = [&](size_t budget) {
     for (int cap = 1024; cap >= 8; cap -= 8) {
       const ChunkCaps c{cap, cap, cap, P->ks->meta_bytes(cap, cap, cap)};
