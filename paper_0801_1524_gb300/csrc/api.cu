@@ -259,9 +259,11 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
         lanes_issued += ((nf + 31) / 32 + (nf2 + 31) / 32) * 32;
       }
     }
-    double fib_p2 = 1.0;  // fibres x p^2 complex multiply-adds per source, 8 flops each
-    for (int d = 0; d < dim + 1; ++d) fib_p2 *= p;
-    I.flops_fwd += (double)srcs * fib_p2 * 8.0;
+    // per source and fibre: p (p-1)/2 complex multiply-adds (8 flops) for the columns of
+    // W off the parent nodes, (p+1)/2 complex additions (2 flops) for those on them
+    double fib = 1.0;
+    for (int d = 0; d < dim - 1; ++d) fib *= p;
+    I.flops_fwd += (double)srcs * fib * (8.0 * p * (p - 1) / 2 + 2.0 * (p + 1) / 2);
     lanes_used_all += lanes_used;
     lanes_issued_all += lanes_issued;
   }

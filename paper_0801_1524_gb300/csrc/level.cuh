@@ -186,42 +186,71 @@ __device__ __forceinline__ float2 cmul2(float4 c, float2 x) {
 //   adjoint  y += W(DL)^H x, then, for gamma = 1, y = conj(phi_1) o y (the caller takes
 //            the gamma = 1 source of an item first, so that the scaling applies to that
 //            source alone and no second accumulator is needed).
-// The loops are unrolled: every entry of W and phi has a compile-time address in constant
-// memory.  (Two fibres per lane sharing each entry measured 15-29 % slower: larger
-// unrolled bodies and register pressure.)
+// Half of the child grid points lie on parent grid nodes: tau_l = (DL q + l)/(2q) is the
+// node m' = (DL q + l)/2 when DL q + l is even (q = P - 1 is even), and there the
+// Lagrange weights are the unit vector w(tau_l) = e_{m'} (interpolation property).  Those
+// columns of W (rows of W^H) cost one addition instead of P multiply-adds; only the
+// other entries are read.  The loops are unrolled: the node tests fold at compile time
+// and every remaining entry of W and phi has a compile-time address in constant memory.
+// (Two fibres per lane sharing each entry measured 15-29 % slower: larger unrolled
+// bodies and register pressure.)
 template <typename R, int P, int SK, bool ADJ, int DL>
 __device__ __forceinline__ void apply_factored(bool gamma, const typename Cx<R>::T *X,
                                                typename Cx<R>::T (&y)[P]) {
   using C = typename Cx<R>::T;
+  constexpr int Q = P - 1;
+  static_assert(Q % 2 == 0, "odd p: the child grid's even points are parent nodes");
   C x[P];
 #pragma unroll
   for (int l = 0; l < P; ++l) x[l] = X[l * SK];
-  if constexpr (sizeof(R) == 4) {
-    if (!ADJ && gamma) {
+  if constexpr (!ADJ) {
+    if (gamma) {
 #pragma unroll
-      for (int l = 0; l < P; ++l) x[l] = cmul2(phi_packed<ADJ, DL>(l), x[l]);
+      for (int l = 0; l < P; ++l) {
+        if constexpr (sizeof(R) == 4)
+          x[l] = cmul2(phi_packed<ADJ, DL>(l), x[l]);
+        else
+          x[l] = cmul(phi_entry64<ADJ, DL>(l), x[l]);
+      }
     }
     // l outer, m inner: P independent multiply-add chains in flight
 #pragma unroll
-    for (int l = 0; l < P; ++l)
+    for (int l = 0; l < P; ++l) {
+      if (((DL * Q + l) & 1) == 0) {  // a parent node: a unit column
+        y[(DL * Q + l) >> 1] = cadd(y[(DL * Q + l) >> 1], x[l]);
+      } else {
 #pragma unroll
-      for (int m = 0; m < P; ++m) y[m] = cmac2(w_packed<ADJ, DL>(m, l), x[l], y[m]);
-    if (ADJ && gamma) {
-#pragma unroll
-      for (int m = 0; m < P; ++m) y[m] = cmul2(phi_packed<ADJ, DL>(m), y[m]);
+        for (int m = 0; m < P; ++m) {
+          if constexpr (sizeof(R) == 4)
+            y[m] = cmac2(w_packed<ADJ, DL>(m, l), x[l], y[m]);
+          else
+            y[m] = cfma(w_entry64<ADJ, DL>(m, l), x[l], y[m]);
+        }
+      }
     }
   } else {
-    if (!ADJ && gamma) {
+    // W^H: the rows of the parent nodes are unit rows
 #pragma unroll
-      for (int l = 0; l < P; ++l) x[l] = cmul(phi_entry64<ADJ, DL>(l), x[l]);
-    }
+    for (int r = 0; r < P; ++r)
+      if (((DL * Q + r) & 1) == 0) y[r] = cadd(y[r], x[(DL * Q + r) >> 1]);
 #pragma unroll
     for (int l = 0; l < P; ++l)
 #pragma unroll
-      for (int m = 0; m < P; ++m) y[m] = cfma(w_entry64<ADJ, DL>(m, l), x[l], y[m]);
-    if (ADJ && gamma) {
+      for (int r = 0; r < P; ++r) {
+        if (((DL * Q + r) & 1) == 0) continue;
+        if constexpr (sizeof(R) == 4)
+          y[r] = cmac2(w_packed<ADJ, DL>(r, l), x[l], y[r]);
+        else
+          y[r] = cfma(w_entry64<ADJ, DL>(r, l), x[l], y[r]);
+      }
+    if (gamma) {
 #pragma unroll
-      for (int m = 0; m < P; ++m) y[m] = cmul(phi_entry64<ADJ, DL>(m), y[m]);
+      for (int m = 0; m < P; ++m) {
+        if constexpr (sizeof(R) == 4)
+          y[m] = cmul2(phi_packed<ADJ, DL>(m), y[m]);
+        else
+          y[m] = cmul(phi_entry64<ADJ, DL>(m), y[m]);
+      }
     }
   }
 }
@@ -275,10 +304,8 @@ __device__ __forceinline__ void run_pass(const Item *items, int n_items, int n_t
   }
 }
 
-// FP64 blocks keep twice the registers (two blocks per SM): their operands are twice as wide.
 template <typename R, int D, int P, bool ADJ>
-__global__ void __launch_bounds__(kLevelThreads, sizeof(R) == 4 ? kLevelBlocksPerSm : kLevelBlocksPerSm / 2)
-    level_kernel(const LevelArgs a) {
+__global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel(const LevelArgs a) {
   using C = typename Cx<R>::T;
   using S = LevelShape<R, D, P>;
   constexpr int TS = S::TS;
