@@ -287,16 +287,27 @@ __device__ __forceinline__ void run_pass(const Item *items, int n_items, int n_t
     C y[P];
 #pragma unroll
     for (int m = 0; m < P; ++m) y[m] = cmk((R)0, (R)0);
-    const int nsrc = fl < nfib2 ? 2 : 1;
-#pragma unroll 1
-    for (int jj = 0; jj < nsrc; ++jj) {
-      const int j = (ADJ && nsrc == 2) ? 1 - jj : jj;  // adjoint: the gamma = 1 source first
-      const int op = j ? it.ops >> 2 : it.ops & 3;
-      const C *X = src + (size_t)(j ? it.src1 : it.src0) * TS + base;
-      if (op & 1)
-        apply_factored<R, P, SK, ADJ, 1>((op >> 1) != 0, X, y);
-      else
-        apply_factored<R, P, SK, ADJ, 0>((op >> 1) != 0, X, y);
+    const C *X0 = src + (size_t)it.src0 * TS + base;
+    const bool d0 = (it.ops & 1) != 0, g0 = (it.ops & 2) != 0;
+    if (fl < nfib2) {
+      // two sources: forward, the delta = 0 and delta = 1 children of the same gamma;
+      // adjoint, the gamma = 0 and gamma = 1 children of the same delta (gamma = 1
+      // first, so that its scaling applies to it alone)
+      const C *X1 = src + (size_t)it.src1 * TS + base;
+      if constexpr (!ADJ) {
+        apply_factored<R, P, SK, ADJ, 0>(g0, X0, y);
+        apply_factored<R, P, SK, ADJ, 1>(g0, X1, y);
+      } else if (d0) {
+        apply_factored<R, P, SK, ADJ, 1>(true, X1, y);
+        apply_factored<R, P, SK, ADJ, 1>(false, X0, y);
+      } else {
+        apply_factored<R, P, SK, ADJ, 0>(true, X1, y);
+        apply_factored<R, P, SK, ADJ, 0>(false, X0, y);
+      }
+    } else if (d0) {
+      apply_factored<R, P, SK, ADJ, 1>(g0, X0, y);
+    } else {
+      apply_factored<R, P, SK, ADJ, 0>(g0, X0, y);
     }
     C *Y = dst + (size_t)it.dst * TS + base;
 #pragma unroll
