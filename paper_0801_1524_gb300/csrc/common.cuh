@@ -62,6 +62,35 @@ __device__ __forceinline__ C shfl_xor_c(C a, int mask) {
   return a;
 }
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with the
+// programmatic stream-serialisation attribute (launch_dependent below) may be scheduled
+// while its predecessor in the stream is still draining.  pdl_wait() returns once the
+// predecessor grid has completed and its memory operations are visible; every thread
+// calls it before its first access to memory that an earlier kernel writes or reads.
+// pdl_trigger() lets the successor be scheduled before this grid ends.  Both are no-ops
+// in a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+// Launches kernel k with the programmatic stream-serialisation attribute set.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                             Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<Args &&>(args)...);
+}
+
 // Loads element i of an interleaved complex array of float or double as C.
 template <typename C>
 __device__ __forceinline__ C load_io(const void *p, int64_t i, bool io64) {

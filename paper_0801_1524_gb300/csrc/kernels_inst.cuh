@@ -68,11 +68,8 @@ struct Impl {
   using S = LevelShape<R, D, P>;
   static cudaError_t level(const LevelArgs &a, bool adjoint, int grid, size_t smem, cudaStream_t s) {
     if (a.nchunks <= 0) return cudaSuccess;
-    if (adjoint)
-      level_kernel<R, D, P, true><<<grid, kLevelThreads, smem, s>>>(a);
-    else
-      level_kernel<R, D, P, false><<<grid, kLevelThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_dependent(adjoint ? level_kernel<R, D, P, true> : level_kernel<R, D, P, false>,
+                            dim3(grid), dim3(kLevelThreads), smem, s, a);
   }
   static cudaError_t level_setup(size_t smem, int *blocks) {
     // The limit is a property of the kernel function, shared by every plan on the device:
@@ -103,15 +100,13 @@ struct Impl {
     if (work == 0) return cudaSuccess;
     constexpr int64_t E = kPointThreads * kSpreadPerThread;
     dim3 grid((unsigned)((work + E - 1) / E), (unsigned)a.nrhs);
-    spread_kernel<R, D, P><<<grid, kPointThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_dependent(spread_kernel<R, D, P>, grid, dim3(kPointThreads), 0, s, a);
   }
   static cudaError_t interp(const PointArgs &a, cudaStream_t s) {
     if (a.n_total == 0) return cudaSuccess;
     const int64_t lanes = a.n_total * kInterpLanes;
     dim3 grid((unsigned)((lanes + kPointThreads - 1) / kPointThreads), (unsigned)a.nrhs);
-    interp_kernel<R, D, P><<<grid, kPointThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_dependent(interp_kernel<R, D, P>, grid, dim3(kPointThreads), 0, s, a);
   }
   static const KernelSet *get() {
     static const KernelSet ks = {&level,         &level_setup,  &level_smem, &meta_bytes,

@@ -341,6 +341,9 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
+  // The next stage's blocks may be scheduled now: they take the slots of this grid's
+  // blocks as these exit and wait for this grid's outputs (pdl_wait) before their copies.
+  pdl_trigger();
 
   const int my_chunks = blockIdx.x < a.nchunks ? (a.nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int n_work = my_chunks * a.nrhs;
@@ -350,7 +353,7 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
   if (warp == kConsumerWarps) {
     // ---------------- producer warp: write-back of chunk it-2, then copies of chunk it
     int issued[2] = {-1, -1};
-    bool failed = false;
+    bool failed = false, waited = false;
     // writes back the outputs staged in slot s by work item `prev`; false on a timeout
     auto write_back = [&](int s, int prev) -> bool {
       const int use = prev >> 1;
@@ -401,6 +404,11 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
         bulk_g2s(meta_s, blob + cd.blob_off, (unsigned)cd.blob_bytes, &full[s]);
       }
       __syncwarp();
+      if (!waited) {
+        // the first chunk's program is in flight; its inputs are the predecessor's outputs
+        pdl_wait();
+        waited = true;
+      }
       const unsigned char *rin = ibase + (size_t)r * irhs * sizeof(C);
       for (int j = lane; j < cd.n_runs; j += 32) {
         const Run rn = runs[cd.run_off + j];
@@ -412,6 +420,7 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
     // the last two chunks' outputs
     for (int it = (n_work >= 2 ? n_work - 2 : 0); it < n_work && !failed; ++it)
       if (issued[it & 1] == it && !write_back(it & 1, it)) failed = true;
+    if (!waited) pdl_wait();
     if (failed && lane == 0) atomicOr(a.status, 1);
     // copies still in flight land before the block exits
     for (int s = 0; s < 2; ++s) {
@@ -422,7 +431,8 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
     return;
   }
 
-  // ---------------- consumer warps
+  // ---------------- consumer warps (shared memory only, but for the status word)
+  pdl_wait();
   for (int it = 0; it < n_work; ++it) {
     const int s = it & 1, use = it >> 1;
     const bool ok = mbar_wait(&full[s], use & 1, a.wait_limit);

@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(kPointThreads) spread_kernel(const PointArgs a
     j1[k] = on ? a.leaf_start[bk[k] + 1] : 0;
     acc[k] = cmk((R)0, (R)0);
   }
+  pdl_trigger();
+  pdl_wait();  // the point values and the output tiles belong to the predecessor's stream
   // the block's points: those of leaves e0/PD .. (last element)/PD
   const int64_t e1 = min(n_el, e0 + E);
   const int jb0 = a.leaf_start[e0 / PD], jb1 = a.leaf_start[(e1 - 1) / PD + 1];
@@ -102,13 +104,18 @@ __global__ void __launch_bounds__(kPointThreads) interp_kernel(const PointArgs a
   const int r = blockIdx.y;
   const bool active = i < a.n_total;
   C acc = cmk((R)0, (R)0);
-  if (active) {
-    const C *Wi = reinterpret_cast<const C *>(a.W) + (size_t)i * D * P;
-    const C *tile = reinterpret_cast<const C *>(a.vin) + (size_t)r * a.tile_rhs +
-                    (size_t)a.point_leaf[i] * a.tile_stride;
-    C wl[P];  // weights of the last axis
+  // the plan's weights and leaf indices are read before the predecessor grid has ended;
+  // the tiles it writes after
+  pdl_trigger();
+  const C *Wi = reinterpret_cast<const C *>(a.W) + (size_t)(active ? i : 0) * D * P;
+  const C *tile = reinterpret_cast<const C *>(a.vin) + (size_t)r * a.tile_rhs +
+                  (size_t)(active ? a.point_leaf[i] : 0) * a.tile_stride;
+  C wl[P];  // weights of the last axis
 #pragma unroll
-    for (int l = 0; l < P; ++l) wl[l] = a.conj ? cconj(Wi[(D - 1) * P + l]) : Wi[(D - 1) * P + l];
+  for (int l = 0; l < P; ++l)
+    wl[l] = !active ? cmk((R)0, (R)0) : a.conj ? cconj(Wi[(D - 1) * P + l]) : Wi[(D - 1) * P + l];
+  pdl_wait();
+  if (active) {
 #pragma unroll
     for (int h = 0; h < (P + kInterpLanes - 1) / kInterpLanes; ++h) {
       const int l0 = g + h * kInterpLanes;
