@@ -226,6 +226,25 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   }
   P->caps = caps;
   P->level_smem = P->ks->level_smem(caps);
+  // the persistent grid of the recursive step (resident blocks per SM x SMs), for which
+  // the stage programs are scheduled
+  if (!host_only) {
+    int blocks = 0, sms = 0;
+    cudaError_t e = P->ks->level_setup(P->level_smem, &blocks);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
+    if (e != cudaSuccess) {
+      delete P;
+      return fail(BFLY_ERR_CUDA, std::string("recursive-step setup: ") + cudaGetErrorString(e));
+    }
+    if (blocks < 1) {
+      const std::string msg = "recursive-step kernel cannot be resident with " +
+                              std::to_string(P->level_smem) + " bytes of shared memory";
+      delete P;
+      return fail(BFLY_ERR_UNSUPPORTED, msg);
+    }
+    P->level_grid = blocks * sms;
+    I.blocks_per_sm = blocks;
+  }
   P->progF.resize(L);
   P->progA.resize(L);
   int64_t lanes_used_all = 0, lanes_issued_all = 0;
@@ -335,6 +354,8 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   }
   static const int zero_status = 0;
   A.add(reinterpret_cast<void **>(&P->status), sizeof(int), &zero_status);
+  const std::vector<unsigned long long> zero_sched((size_t)4 * std::max(L, 1), 0ull);
+  A.add_vec(&P->sched, zero_sched);
   const size_t buf_bytes = (size_t)maxp * P->TS * P->elem_bytes * o.max_nrhs;
   A.add(&P->buf[0], buf_bytes);
   A.add(&P->buf[1], buf_bytes);
@@ -362,25 +383,13 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     e = bfly::launch_weights(o.prec == BFLY_PREC_FP64 ? 0 : 1, nk, dim, p, 0, P->off_k, P->inv_den, P->Wk, 0);
   if (e == cudaSuccess)
     e = bfly::launch_weights(o.prec == BFLY_PREC_FP64 ? 0 : 1, nx, dim, p, 1, P->off_x, P->inv_den, P->Wx, 0);
-  int blocks = 0;
-  if (e == cudaSuccess) e = P->ks->level_setup(P->level_smem, &blocks);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
-  int sms = 0;
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, P->device);
   if (e != cudaSuccess) {
     const std::string msg = std::string("plan upload: ") + cudaGetErrorString(e);
     bfly_plan_destroy(P);
     return fail(BFLY_ERR_CUDA, msg);
   }
-  if (blocks < 1) {
-    const std::string msg = "recursive-step kernel cannot be resident with " +
-                            std::to_string(P->level_smem) + " bytes of shared memory";
-    bfly_plan_destroy(P);
-    return fail(BFLY_ERR_UNSUPPORTED, msg);
-  }
-  P->level_grid = blocks * sms;
   I.smem_kb = (int)((P->level_smem + 1023) / 1024);
-  I.blocks_per_sm = blocks;
   I.workspace_bytes = (int64_t)P->dbytes;
   I.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   *out = P;

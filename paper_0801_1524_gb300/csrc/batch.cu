@@ -21,6 +21,7 @@ struct bfly_batch_s {
   std::vector<bfly::BatchEntry *> entries;  // per stage t
   std::vector<int> n_entries;
   int *status = nullptr;
+  unsigned long long *sched = nullptr;  // work counters of the stage launches, [t][2]
   // graph of the last execute: replayed when the key matches
   cudaGraphExec_t exec = nullptr;
   std::vector<const void *> key_f;
@@ -69,6 +70,7 @@ bfly_status launch_all(bfly_batch_t B, const void *const *f, void *const *u, int
     a.meta_bytes = B->meta_bytes;
     a.wait_limit = 2000000000LL;  // ~1 s of SM clock
     a.status = B->status;
+    a.sched = B->sched + (size_t)t * 2;
     BATCH_CUDA(P0->ks->level(a, false, B->grid, B->smem, s));
   }
   for (int i = 0; i < B->count; ++i) {
@@ -133,11 +135,13 @@ bfly_status bfly_batch_create(bfly_batch_t *out, int count, const bfly_plan_t *p
   }
   // entries of every stage, all plans
   std::vector<std::vector<bfly::BatchEntry>> host(B->L_max);
-  for (int t = 0; t < B->L_max; ++t)
+  for (int t = 0; t < B->L_max; ++t) {
+    std::vector<double> work;  // the chunks of every plan, scheduled together
     for (auto *P : B->plans) {
       if (t >= P->L) continue;
       const bfly::StageProgram &pg = P->progF[t];
       for (const bfly::ChunkDesc &cd : pg.chunks) {
+        work.push_back(bfly::chunk_work(pg.blob.data() + cd.blob_off, B->dim, B->p));
         bfly::BatchEntry e;
         e.d = cd;
         e.blob = P->dF[t].blob;
@@ -149,7 +153,13 @@ bfly_status bfly_batch_create(bfly_batch_t *out, int count, const bfly_plan_t *p
         host[t].push_back(e);
       }
     }
-  size_t total = 256;  // status word
+    const std::vector<size_t> order = bfly::schedule_chunks(work);
+    std::vector<bfly::BatchEntry> sorted(host[t].size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = host[t][order[i]];
+    host[t].swap(sorted);
+  }
+  const size_t sched_bytes = ((size_t)B->L_max * 2 * sizeof(unsigned long long) + 255) & ~(size_t)255;
+  size_t total = 256 + sched_bytes;  // status word, work counters
   for (auto &v : host) total += (v.size() * sizeof(bfly::BatchEntry) + 255) & ~(size_t)255;
   cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&B->dmem), total);
   if (e != cudaSuccess) {
@@ -160,6 +170,9 @@ bfly_status bfly_batch_create(bfly_batch_t *out, int count, const bfly_plan_t *p
   B->status = reinterpret_cast<int *>(B->dmem);
   e = cudaMemset(B->status, 0, sizeof(int));
   at += 256;
+  B->sched = reinterpret_cast<unsigned long long *>(B->dmem + at);
+  if (e == cudaSuccess) e = cudaMemset(B->sched, 0, sched_bytes);
+  at += sched_bytes;
   B->entries.assign(B->L_max, nullptr);
   B->n_entries.assign(B->L_max, 0);
   for (int t = 0; t < B->L_max && e == cudaSuccess; ++t) {

@@ -136,6 +136,9 @@ struct LevelArgs {
   int *status;                  // device status word: bits set on a timeout
   int inject_stall;             // test hook: withhold the copies of the first chunk
   const BatchEntry *entries;    // batched launch: per-chunk chunk and buffers (else null)
+  // work counter of the launch {items taken after the first round, blocks done}: zero at
+  // launch, reset by the last block to finish (one per stage and direction)
+  unsigned long long *sched;
 };
 
 // Steps 2 and 4 and their adjoints: per-point weights against one tile per leaf.

@@ -45,6 +45,7 @@ __host__ __device__ constexpr int tile_stride(int pd) {
 }
 
 constexpr int kConsumerWarps = 7;  // + 1 producer: 8 warps, two per SM sub-partition
+static_assert(kConsumerWarps == kProgramWarps, "the chunk programs are balanced for this count");
 constexpr int kLevelThreads = (kConsumerWarps + 1) * 32;
 constexpr int kLevelBlocksPerSm = 4;
 
@@ -324,6 +325,7 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
   unsigned char *ptr = smem;
   uint64_t *full = reinterpret_cast<uint64_t *>(ptr);  // full[2], staged[2]
   uint64_t *staged = full + 2;
+  int *end_it = reinterpret_cast<int *>(full + 4);  // first iteration without work
   ptr += 64;
   unsigned char *meta0 = ptr;  // slot s at meta0 + s * meta_bytes
   ptr += 2 * (size_t)a.meta_bytes;
@@ -338,6 +340,7 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
     mbar_init(&full[1], 1);
     mbar_init(&staged[0], 1);
     mbar_init(&staged[1], 1);
+    *end_it = 0x7fffffff;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
@@ -345,20 +348,28 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
   // blocks as these exit and wait for this grid's outputs (pdl_wait) before their copies.
   pdl_trigger();
 
-  const int my_chunks = blockIdx.x < a.nchunks ? (a.nchunks - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int n_work = my_chunks * a.nrhs;
   const unsigned char *gin = reinterpret_cast<const unsigned char *>(a.in);
   unsigned char *gout = reinterpret_cast<unsigned char *>(a.out);
 
   if (warp == kConsumerWarps) {
-    // ---------------- producer warp: write-back of chunk it-2, then copies of chunk it
-    int issued[2] = {-1, -1};
+    // ---------------- producer warp.  Work items w = chunk * nrhs + rhs, the chunks in
+    // decreasing work: block b first takes item b, then the next untaken item of the
+    // launch's counter (gridDim.x + a.sched[0]), so that the blocks finish together.
+    // Iteration it uses slot it mod 2: write-back of the outputs of iteration it-2, then
+    // the copies of the new item.
+    const long long total = (long long)a.nchunks * a.nrhs;
+    int slot_it[2] = {-1, -1};        // iteration whose outputs slot s holds, -1: none
+    long long slot_w[2] = {-1, -1};   // its work item
+    int phase_it[2] = {-1, -1};       // last iteration that completes a phase of full[s]
     bool failed = false, waited = false;
-    // writes back the outputs staged in slot s by work item `prev`; false on a timeout
-    auto write_back = [&](int s, int prev) -> bool {
-      const int use = prev >> 1;
-      const bool ok = mbar_wait(&staged[s], use & 1, a.wait_limit);
-      if (!__all_sync(0xffffffffu, ok)) return false;
+    // writes back the outputs staged in slot s by iteration `prev` (item w); false on a
+    // timeout
+    auto wait_staged = [&](int s, int prev) -> bool {
+      const bool ok = mbar_wait(&staged[s], (prev >> 1) & 1, a.wait_limit);
+      return __all_sync(0xffffffffu, ok);
+    };
+    // writes back the outputs staged in slot s by item w (after wait_staged)
+    auto write_back = [&](int s, long long w) {
       const unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
       const int32_t *hdr = reinterpret_cast<const int32_t *>(meta_s);
       const int n_items = hdr[0] + hdr[1] + hdr[2], n_oruns = hdr[7];
@@ -368,11 +379,11 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
       unsigned char *obase = gout;
       int64_t orhs = a.out_rhs;
       if (a.entries) {
-        const BatchEntry &be = a.entries[blockIdx.x + (prev / a.nrhs) * gridDim.x];
+        const BatchEntry &be = a.entries[w / a.nrhs];
         obase = reinterpret_cast<unsigned char *>(be.out);
         orhs = be.out_rhs;
       }
-      unsigned char *rout = obase + (size_t)(prev % a.nrhs) * orhs * sizeof(C);
+      unsigned char *rout = obase + (size_t)(w % a.nrhs) * orhs * sizeof(C);
       for (int j = lane; j < n_oruns; j += 32) {
         const Run rn = oruns[j];
         bulk_s2g(rout + (size_t)rn.start * S::tile_bytes, stage + (size_t)rn.slot * S::tile_bytes,
@@ -381,21 +392,44 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
       bulk_commit();
       bulk_wait_read();  // the slot may be refilled after this
       __syncwarp();
-      return true;
     };
-    for (int it = 0; it < n_work && !failed; ++it) {
+    int it = 0;
+    for (;; ++it) {
       const int s = it & 1;
-      if (it >= 2 && !write_back(s, it - 2)) {
+      const bool wb = slot_it[s] >= 0;
+      if (wb && !wait_staged(s, slot_it[s])) {
         failed = true;
         break;
       }
-      const int ch = blockIdx.x + (it / a.nrhs) * gridDim.x, r = it % a.nrhs;
+      // the next item; a counter's latency overlaps the write-back's stores
+      long long w = blockIdx.x;
+      if (it > 0 && lane == 0) w = (long long)gridDim.x + (long long)atomicAdd(a.sched, 1ull);
+      if (wb) {
+        write_back(s, slot_w[s]);
+        slot_it[s] = -1;
+      }
+      w = __shfl_sync(0xffffffffu, w, 0);
+      if (w >= total) {
+        // no more work: the consumers stop at iteration it (the phase completes without
+        // data)
+        if (lane == 0) {
+          *end_it = it;
+          mbar_arrive(&full[s]);
+        }
+        phase_it[s] = it;
+        __syncwarp();
+        break;
+      }
+      const long long ch = w / a.nrhs;
+      const int r = (int)(w % a.nrhs);
       const ChunkDesc cd = a.entries ? a.entries[ch].d : a.chunks[ch];
       const unsigned char *blob = a.entries ? a.entries[ch].blob : a.blob;
       const Run *runs = a.entries ? a.entries[ch].runs : a.runs;
       const unsigned char *ibase =
           a.entries ? reinterpret_cast<const unsigned char *>(a.entries[ch].in) : gin;
       const int64_t irhs = a.entries ? a.entries[ch].in_rhs : a.in_rhs;
+      slot_it[s] = it;
+      slot_w[s] = w;
       if (a.inject_stall && it == 0) continue;  // test hook: the first chunk never arrives
       unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
       unsigned char *in_s = reinterpret_cast<unsigned char *>(slot0 + (size_t)s * a.cap0 * TS);
@@ -415,31 +449,43 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
         bulk_g2s(in_s + (size_t)rn.slot * S::tile_bytes, rin + (size_t)rn.start * S::tile_bytes,
                  (unsigned)(rn.count * S::tile_bytes), &full[s]);
       }
-      issued[s] = it;
+      phase_it[s] = it;
     }
-    // the last two chunks' outputs
-    for (int it = (n_work >= 2 ? n_work - 2 : 0); it < n_work && !failed; ++it)
-      if (issued[it & 1] == it && !write_back(it & 1, it)) failed = true;
+    // the outputs of the iteration before the last
+    const int sl = (it + 1) & 1;
+    if (!failed && slot_it[sl] >= 0) {
+      if (wait_staged(sl, slot_it[sl])) write_back(sl, slot_w[sl]);
+      else failed = true;
+    }
     if (!waited) pdl_wait();
     if (failed && lane == 0) atomicOr(a.status, 1);
     // copies still in flight land before the block exits
     for (int s = 0; s < 2; ++s) {
-      const bool ok = issued[s] < 0 || mbar_wait(&full[s], (issued[s] >> 1) & 1, a.wait_limit);
+      const bool ok = phase_it[s] < 0 || mbar_wait(&full[s], (phase_it[s] >> 1) & 1, a.wait_limit);
       if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(a.status, 2);
     }
     bulk_wait_all();  // outputs written before the block exits
+    if (lane == 0) {
+      // the last block done with the counter resets it for the next launch of this stage
+      __threadfence();
+      if (atomicAdd(&a.sched[1], 1ull) == (unsigned long long)gridDim.x - 1) {
+        atomicExch(&a.sched[0], 0ull);
+        atomicExch(&a.sched[1], 0ull);
+      }
+    }
     return;
   }
 
   // ---------------- consumer warps (shared memory only, but for the status word)
   pdl_wait();
-  for (int it = 0; it < n_work; ++it) {
+  for (int it = 0;; ++it) {
     const int s = it & 1, use = it >> 1;
     const bool ok = mbar_wait(&full[s], use & 1, a.wait_limit);
     if (consumer_any(!ok)) {  // every consumer warp leaves together
       if (tid == 0) atomicOr(a.status, 4);
       break;
     }
+    if (it == *static_cast<volatile int *>(end_it)) break;  // written before that phase completed
     const unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
     C *in_s = slot0 + (size_t)s * a.cap0 * TS;
     C *scr = scr0 + (size_t)(s % S::NSCR) * a.cap1 * TS;

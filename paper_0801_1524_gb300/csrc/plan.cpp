@@ -381,7 +381,39 @@ StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp
     }
   }
   flush();
+  // the order in which the blocks of a launch take the chunks
+  const size_t n = prog.chunks.size();
+  std::vector<double> work(n);
+  for (size_t c = 0; c < n; ++c) work[c] = chunk_work(prog.blob.data() + prog.chunks[c].blob_off, dim, p);
+  const std::vector<size_t> order = schedule_chunks(work);
+  std::vector<ChunkDesc> chunks(n);
+  std::vector<int32_t> in_off(n);
+  for (size_t c = 0; c < n; ++c) {
+    chunks[c] = prog.chunks[order[c]];
+    in_off[c] = prog.in_off[order[c]];
+  }
+  prog.chunks.swap(chunks);
+  prog.in_off.swap(in_off);
   return prog;
+}
+
+std::vector<size_t> schedule_chunks(const std::vector<double> &work) {
+  std::vector<size_t> order(work.size());
+  std::iota(order.begin(), order.end(), (size_t)0);
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
+  return order;
+}
+
+double chunk_work(const unsigned char *blob_header, int dim, int p) {
+  const int32_t *hdr = reinterpret_cast<const int32_t *>(blob_header);
+  int64_t fib = 1;
+  for (int d = 1; d < dim; ++d) fib *= p;
+  double w = 1.0;
+  for (int k = 0; k < dim; ++k) {
+    const int64_t nf = hdr[k] * fib, nf2 = hdr[3 + k] * fib;
+    w += (double)((nf + 31) / 32 + (nf2 + 31) / 32) / kProgramWarps;
+  }
+  return w;
 }
 
 std::string validate_program(const StageProgram &prog, int dim, int p, ChunkCaps caps, int64_t in_tiles,

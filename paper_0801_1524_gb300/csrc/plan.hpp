@@ -14,6 +14,8 @@ namespace bfly {
 // to 16 bytes) is copied to shared memory in one piece; its inputs are copied run by run,
 // its outputs written back run by run.
 constexpr int kBlobHeader = 32;
+// Consumer warps of a recursive-step block, which split every pass of a chunk.
+constexpr int kProgramWarps = 7;
 struct ChunkDesc {
   int32_t blob_off;   // byte offset of the blob in StageProgram::blob (16-byte aligned)
   int32_t blob_bytes; // multiple of 16
@@ -117,9 +119,21 @@ void leaf_weights(int p, double tau, double *w /* 2p doubles */);
 //   csAp : children of the A' boxes (T_X level L-t-1 -> L-t), xidx: box indices of level L-t
 //   csB  : children of the B boxes (T_K level t -> t+1),       kidx: box indices of level t+1
 //   in_row / out_row: tiles per row of the input / output stage buffer.
+// The chunks are runs of consecutive units, each as large as the capacities allow, listed
+// in the order of schedule_chunks.
 StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp,
                                 const std::vector<int32_t> &xidx, const std::vector<int32_t> &csB,
                                 const std::vector<int32_t> &kidx, bool adjoint, ChunkCaps caps);
+
+// The order in which the persistent blocks of a launch take the chunks (indices into
+// work): decreasing work, so that the blocks that finish first take the smallest chunks
+// last (longest processing time first).
+std::vector<size_t> schedule_chunks(const std::vector<double> &work);
+
+// Estimated work of a chunk from its blob header: one unit per chunk (waits, barriers)
+// plus, per pass, the 32-lane steps of its fibres (two-source fibres count twice) over
+// the kProgramWarps consumer warps that share them.
+double chunk_work(const unsigned char *blob_header, int dim, int p);
 
 // Checks every index of a compiled stage program against the capacities it was compiled
 // for and the number of tiles of its input and output stage buffers; returns "" or a

@@ -36,6 +36,8 @@ struct bfly_plan_s {
     bfly::Run *runs = nullptr;
   };
   int *status = nullptr;  // device status word (bfly_device_status)
+  // work counters of the recursive-step launches, [direction][stage t][2] (LevelArgs::sched)
+  unsigned long long *sched = nullptr;
   std::vector<DevProg> dF, dA;  // per stage t in [0, L-1]
   void *buf[2] = {nullptr, nullptr};
   void *stage_in = nullptr, *stage_out = nullptr;
@@ -89,6 +91,7 @@ inline bfly::LevelArgs level_args(bfly_plan_t P, int t, bool adjoint, int nrhs) 
   a.wait_limit = stall ? 2000000LL : 2000000000LL;  // ~1 ms / ~1 s of SM clock
   a.status = P->status;
   a.inject_stall = stall ? 1 : 0;
+  a.sched = P->sched + ((adjoint ? (size_t)P->L : 0) + (size_t)t) * 2;
   return a;
 }
 
