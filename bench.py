@@ -1,8 +1,8 @@
 #!/usr/bin/env python3
 """Benchmark of the butterfly sparse Fourier transform on one GB300.
 
-Workload (one "step" = one whole transform: leaf step, the L recursive stages, final
-step): 2D, N = 8192, X = circle of radius 0.4 (82,355 targets), K = ellipse 0.45 x 0.3
+Workload (one "step" = one whole transform: leaf step, the L recursive stages in one- or
+two-stage launches, final step): 2D, N = 8192, X = circle of radius 0.4 (82,355 targets), K = ellipse 0.45 x 0.3
 with a 0.03 sin(5 theta) radial perturbation (80,962 sources), p = 7, one right-hand side
 of complex64 Gaussian sources, FP32 arithmetic with FP64-built operators.
 
@@ -184,6 +184,23 @@ def replica_value(world, ms):
 
 
 # ---------------------------------------------------------------------------- main arm
+def step_stages(L, dim, S):
+    """(t, levels) of the recursive-step launches when the plan follows the default split
+    (2D: stage L-1 alone when L is odd, then pairs down to (1, 0); 3D: one stage each),
+    else None."""
+    if dim == 3:
+        out = [(t, 1) for t in range(L - 1, -1, -1)]
+    else:
+        out, t = [], L - 1
+        if L % 2 == 1:
+            out.append((t, 1))
+            t -= 1
+        while t >= 1:
+            out.append((t, 2))
+            t -= 2
+    return out if len(out) == S else None
+
+
 def main_bfly(args, rank, world, dist):
     import torch
     from paper_0801_1524_gb300.plan import Plan
@@ -199,11 +216,12 @@ def main_bfly(args, rank, world, dist):
     plan = Plan(inst.x, inst.k, inst.N, inst.p, precision="fp32", smem_kb=args.smem_kb)
     info = plan.info()
     L = info["L"]
+    S = info["steps"]    # recursive-step launches per transform
     u = torch.empty(nx, dtype=torch.complex64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def new_events():
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(L + 3)]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(S + 3)]
         for e in evs:
             e.record(stream)
         return evs
@@ -247,8 +265,8 @@ def main_bfly(args, rank, world, dist):
         flush_l2(flush)
         plan.with_events(f, events[k], out=u)
     torch.cuda.synchronize()
-    level_ms = [ev[1].elapsed_time(ev[L + 1]) for ev in events]
-    kern_ms = np.array([[ev[i].elapsed_time(ev[i + 1]) for i in range(L + 2)] for ev in events])
+    level_ms = [ev[1].elapsed_time(ev[S + 1]) for ev in events]
+    kern_ms = np.array([[ev[i].elapsed_time(ev[i + 1]) for i in range(S + 2)] for ev in events])
     ms = max_over_ranks(float(np.mean(step_ms)), dist, dev)
     clk = clocks.stop() if clocks else None
 
@@ -335,39 +353,47 @@ def main_bfly(args, rank, world, dist):
                            "eps_a_fp32_vs_gpu_direct_fp64": eps_a32}
         del plan64
 
-    # ---- roofline of the recursive step (the dominant kernel: L launches per step)
+    # ---- roofline of the recursive step (the dominant kernel: S launches per step)
     d, p = inst.dim, inst.p
     PD = p ** d
     # algorithmic units of the recursive step, all stages, one RHS: per (pair, child)
-    # 2p^3 complex multiply-adds in 2D (3p^4 in 3D), 8 real flops each; every stage's
-    # tiles read once and written once (p^d complex64 each)
+    # 2p^3 complex multiply-adds in 2D (3p^4 in 3D), 8 real flops each; the tiles of the
+    # stages between launches read once and written once (p^d complex64 each; the stage
+    # inside a two-stage launch stays in shared memory)
     flops = info["jobs_fwd"] * (2 * p ** 3 if d == 2 else 3 * p ** 4) * 8.0
     flops_exec = info["flops_fwd"]     # as executed (sum factorisation shares work)
-    bytes_ = (info["tiles_read_fwd"] + info["tiles_written_fwd"]) * PD * 8.0
+    steps = step_stages(L, d, S)
+    pairs = {t: a * b for t, a, b in plan.stages()}
+    if steps is not None:
+        bytes_ = sum(pairs[t + 1] + pairs[t - lev + 1] for t, lev in steps) * PD * 8.0
+    else:
+        bytes_ = (info["tiles_read_fwd"] + info["tiles_written_fwd"]) * PD * 8.0
     level_s = float(np.mean(level_ms)) * 1e-3
-    per_launch_s = level_s / L
+    per_launch_s = level_s / S
     hbm_peak, hbm_src = peaks()
     alu_peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12   # TFLOP/s
-    a_alu = flops / L / per_launch_s / 1e12
-    a_hbm = bytes_ / L / per_launch_s / 1e9
+    a_alu = flops / S / per_launch_s / 1e12
+    a_hbm = bytes_ / S / per_launch_s / 1e9
     roof_alu = {"bound": "alu", "achieved": a_alu, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": a_alu / alu_peak, "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
     roof_hbm = {"bound": "hbm", "achieved": a_hbm, "peak": hbm_peak, "unit": "GB/s",
                 "frac": a_hbm / hbm_peak, "traffic": None,
                 "peak_source": f"{hbm_src} copy bandwidth"}
-    traffic = level_traffic(per_launch_bytes=bytes_ / L)
+    traffic = level_traffic(per_launch_bytes=bytes_ / S)
     main, alt = (roof_alu, roof_hbm) if roof_alu["frac"] >= roof_hbm["frac"] else (roof_hbm, roof_alu)
     main["traffic"] = traffic
     alt["traffic"] = traffic
-    main["kernel"] = f"level_kernel<float,{d},{p}> (recursive step, one launch per stage)"
-    main["algorithmic_per_launch"] = {"flops": flops / L, "bytes": bytes_ / L,
-                                      "executed_flops": flops_exec / L}
+    main["kernel"] = (f"level_kernel<float,{d},{p}> (recursive step, {S} launches: "
+                      + ("one or two stages each)" if d == 2 else "one stage each)"))
+    main["algorithmic_per_launch"] = {"flops": flops / S, "bytes": bytes_ / S,
+                                      "executed_flops": flops_exec / S}
     main["duration"] = ("mean per-launch CUDA-event time of the recursive step, from a second pass "
                         "of the same steps with an event between consecutive launches")
     alt["kernel"] = main["kernel"]
     out["roofline_alt"] = alt
-    kern_names = ["leaf"] + [f"level_t{t}" for t in range(L - 1, -1, -1)] + ["final"]
+    kern_names = (["leaf"] + ([f"level_t{t}" + (f"-{t - 1}" if lev == 2 else "") for t, lev in steps]
+                              if steps is not None else [f"level_{i}" for i in range(S)]) + ["final"])
     out["kernel_ms"] = {n: float(v) for n, v in zip(kern_names, kern_ms.mean(axis=0))}
 
     value = replica_value(world, ms)
@@ -384,7 +410,7 @@ def main_bfly(args, rank, world, dist):
         "roofline": main,
         "adjoint": {"ms": float(np.mean(adj_ms)), "transforms_per_s": 1e3 / float(np.mean(adj_ms)),
                     "call": "bfly_execute_adjoint (device buffers; the sweep behind the gradient)"},
-        "gpu_launches": args.steps * (L + 2),
+        "gpu_launches": args.steps * (S + 2),
         "clocks": clk,
         "plan": {"seconds": info["plan_seconds"], "L": L, "total_pairs": info["total_pairs"],
                  "max_pairs": info["max_pairs"], "workspace_bytes": info["workspace_bytes"]},

@@ -91,6 +91,8 @@ typedef struct {
   int blocks_per_sm;            /* resident blocks of the recursive step per SM */
   double tuned_ms;              /* autotuning: time of the chosen candidate (0 if not tuned) */
   double plan_seconds;          /* host wall time of bfly_plan_create */
+  int steps;                    /* launches of the recursive step per transform: one or two
+                                   stages each (two where their units fit the capacities) */
 } bfly_plan_info_t;
 
 /*
@@ -167,11 +169,12 @@ bfly_status bfly_direct(bfly_plan_t plan, const void *in, void *out, int nrhs, i
 /*
  * bfly_execute_events — bfly_execute (adjoint = 0) or bfly_execute_adjoint (adjoint = 1)
  * that also records caller-owned CUDA events on `stream`: events[i] just before kernel
- * launch i and events[L+2] after the last launch, so that the elapsed time between
- * events[i] and events[i+1] is the device time of launch i.  Launch order: forward [leaf
- * step, recursive step t = L-1 .. 0, final step]; adjoint [final step adjoint, recursive
- * step t = 0 .. L-1, leaf step adjoint].  n_events must be L + 3; NULL entries are
- * skipped.  Asynchronous like bfly_execute: nothing is synchronised or allocated.
+ * launch i and events[S+2] after the last launch (S = bfly_plan_info_t.steps), so that the
+ * elapsed time between events[i] and events[i+1] is the device time of launch i.  Launch
+ * order: forward [leaf step, the S recursive-step launches for stages L-1 .. 0 (one or
+ * two stages each), final step]; adjoint [final step adjoint, the S launches in reverse,
+ * leaf step adjoint].  n_events must be S + 3; NULL entries are skipped.  Asynchronous
+ * like bfly_execute: nothing is synchronised or allocated.
  */
 bfly_status bfly_execute_events(bfly_plan_t plan, const void *in, void *out, int nrhs,
                                 int dtype, int adjoint, void *stream, void *const *events,

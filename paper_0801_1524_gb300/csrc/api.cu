@@ -245,37 +245,65 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     P->level_grid = blocks * sms;
     I.blocks_per_sm = blocks;
   }
-  P->progF.resize(L);
-  P->progA.resize(L);
+  // steps of the sweep (forward order).  2D: two stages per launch, (1, 0), (3, 2), ...
+  // from the bottom, and stage L-1 alone when L is odd; a pair whose units exceed the
+  // shared-memory capacities runs as two one-stage steps.  3D: one stage per launch (a
+  // two-level unit holds up to 64 input tiles, more than a block's share of shared memory)
+  auto trees = [&](int t) {
+    return bfly::StageTrees{&P->TX.cs[L - t - 1], &P->TX.idx[L - t], &P->TK.cs[t], &P->TK.idx[t + 1]};
+  };
+  std::vector<bfly_plan_s::Step> plan_steps;
+  {
+    int t = L - 1;
+    if (dim == 3)
+      for (; t >= 0; --t) plan_steps.push_back({t, 1});
+    if (L % 2 == 1 && t >= 0) plan_steps.push_back({t--, 1});
+    for (; t >= 1; t -= 2) plan_steps.push_back({t, 2});
+  }
   int64_t lanes_used_all = 0, lanes_issued_all = 0;
-  for (int t = 0; t < L; ++t) {
-    const auto &csAp = P->TX.cs[L - t - 1], &xidx = P->TX.idx[L - t];
-    const auto &csB = P->TK.cs[t], &kidx = P->TK.idx[t + 1];
-    P->progF[t] = bfly::make_stage_program(dim, p, csAp, xidx, csB, kidx, false, caps);
-    P->progA[t] = bfly::make_stage_program(dim, p, csAp, xidx, csB, kidx, true, caps);
+  for (size_t si = 0; si < plan_steps.size(); ++si) {
+    const int t = plan_steps[si].t;
+    bfly::StageProgram pf, pa;
+    bool ok = false;
+    if (plan_steps[si].levels == 2) {
+      const bfly::StageTrees st2[2] = {trees(t), trees(t - 1)};
+      bool fits_f = true, fits_a = true;
+      pf = bfly::make_step_program(dim, p, st2, 2, false, caps, &fits_f);
+      pa = bfly::make_step_program(dim, p, st2, 2, true, caps, &fits_a);
+      ok = fits_f && fits_a;
+      if (!ok) {
+        plan_steps[si].levels = 1;
+        plan_steps.insert(plan_steps.begin() + si + 1, bfly_plan_s::Step{t - 1, 1});
+      }
+    }
+    if (!ok) {
+      const bfly::StageTrees st1 = trees(t);
+      pf = bfly::make_step_program(dim, p, &st1, 1, false, caps);
+      pa = bfly::make_step_program(dim, p, &st1, 1, true, caps);
+    }
+    const int t_lo = t - plan_steps[si].levels + 1;
     for (int dir = 0; dir < 2; ++dir) {
-      const int64_t tin = dir ? P->pairs[t] : P->pairs[t + 1], tout = dir ? P->pairs[t + 1] : P->pairs[t];
-      const std::string bad = bfly::validate_program(dir ? P->progA[t] : P->progF[t], dim, p, caps, tin, tout);
+      const int64_t tin = dir ? P->pairs[t_lo] : P->pairs[t + 1], tout = dir ? P->pairs[t + 1] : P->pairs[t_lo];
+      const std::string bad = bfly::validate_program(dir ? pa : pf, dim, p, caps, tin, tout);
       if (!bad.empty()) {
         delete P;
         return fail(BFLY_ERR_CUDA, "internal error in the stage program: " + bad);
       }
     }
-    I.chunks_fwd += (int64_t)P->progF[t].chunks.size();
-    int64_t lanes_used = 0, lanes_issued = 0;
+    I.chunks_fwd += (int64_t)pf.chunks.size();
     int64_t srcs = 0;  // (output tile of a pass, source) pairs
-    for (const auto &cd : P->progF[t].chunks) {
-      const unsigned char *bp = P->progF[t].blob.data() + cd.blob_off;
+    for (const auto &cd : pf.chunks) {
+      const unsigned char *bp = pf.blob.data() + cd.blob_off;
       const int32_t *hdr = reinterpret_cast<const int32_t *>(bp);
       int64_t ni = 0;
-      for (int k = 0; k < dim; ++k) ni += hdr[k];
+      for (int j = 0; j < hdr[0]; ++j) ni += hdr[4 + j];
       const bfly::Item *it = reinterpret_cast<const bfly::Item *>(bp + bfly::kBlobHeader);
       for (int64_t i = 0; i < ni; ++i) srcs += 1 + (it[i].src1 != 0xffff);
       // lanes used by the steps of every pass (32 fibres per step, two-source fibres first)
-      for (int k = 0; k < dim; ++k) {
-        const int64_t nf = (int64_t)hdr[k] * (PD / p), nf2 = (int64_t)hdr[3 + k] * (PD / p);
-        lanes_used += nf + nf2;
-        lanes_issued += ((nf + 31) / 32 + (nf2 + 31) / 32) * 32;
+      for (int j = 0; j < hdr[0]; ++j) {
+        const int64_t nf = (int64_t)hdr[4 + j] * (PD / p), nf2 = (int64_t)hdr[4 + bfly::kMaxPasses + j] * (PD / p);
+        lanes_used_all += nf + nf2;
+        lanes_issued_all += ((nf + 31) / 32 + (nf2 + 31) / 32) * 32;
       }
     }
     // per source and fibre: p (p-1)/2 complex multiply-adds (8 flops) for the columns of
@@ -283,9 +311,11 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     double fib = 1.0;
     for (int d = 0; d < dim - 1; ++d) fib *= p;
     I.flops_fwd += (double)srcs * fib * (8.0 * p * (p - 1) / 2 + 2.0 * (p + 1) / 2);
-    lanes_used_all += lanes_used;
-    lanes_issued_all += lanes_issued;
+    P->progF.push_back(std::move(pf));
+    P->progA.push_back(std::move(pa));
   }
+  P->steps = plan_steps;
+  I.steps = (int)plan_steps.size();
   I.lane_use_fwd = lanes_issued_all ? (double)lanes_used_all / (double)lanes_issued_all : 1.0;
   if (host_only) {
     I.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -341,12 +371,13 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   }
   A.add(&P->Wx, (size_t)nx * dim * p * P->elem_bytes);
   A.add(&P->Wk, (size_t)nk * dim * p * P->elem_bytes);
-  P->dF.resize(L);
-  P->dA.resize(L);
-  for (int t = 0; t < L; ++t) {
+  const size_t n_steps = P->steps.size();
+  P->dF.resize(n_steps);
+  P->dA.resize(n_steps);
+  for (size_t si = 0; si < n_steps; ++si) {
     for (int dir = 0; dir < 2; ++dir) {
-      StageProgram &pg = dir ? P->progA[t] : P->progF[t];
-      bfly_plan_s::DevProg &dp = dir ? P->dA[t] : P->dF[t];
+      StageProgram &pg = dir ? P->progA[si] : P->progF[si];
+      bfly_plan_s::DevProg &dp = dir ? P->dA[si] : P->dF[si];
       A.add_vec(&dp.chunks, pg.chunks);
       A.add_vec(&dp.blob, pg.blob);
       A.add_vec(&dp.runs, pg.runs);
@@ -354,7 +385,7 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   }
   static const int zero_status = 0;
   A.add(reinterpret_cast<void **>(&P->status), sizeof(int), &zero_status);
-  const std::vector<unsigned long long> zero_sched((size_t)4 * std::max(L, 1), 0ull);
+  const std::vector<unsigned long long> zero_sched((size_t)4 * std::max<size_t>(n_steps, 1), 0ull);
   A.add_vec(&P->sched, zero_sched);
   const size_t buf_bytes = (size_t)maxp * P->TS * P->elem_bytes * o.max_nrhs;
   A.add(&P->buf[0], buf_bytes);
@@ -412,11 +443,11 @@ bfly_status check_exec(bfly_plan_t P, const void *a, const void *b, int nrhs, in
 }
 
 // Launches the sweep on stream s; when ev is non-null, records ev[i] before launch i and
-// ev[L+2] after the last one.
+// ev[steps + 2] after the last one.
 bfly_status run(bfly_plan_t P, const void *in, void *out, int nrhs, int dtype, bool adjoint,
                 cudaStream_t s, cudaEvent_t const *ev = nullptr) {
   const bool io64 = dtype == BFLY_C128;
-  const int L = P->L, PD = P->TS;
+  const int L = P->L, PD = P->TS, S = (int)P->steps.size();
   int n = 0;
   auto mark = [&]() -> cudaError_t {
     cudaEvent_t e = ev ? ev[n++] : nullptr;
@@ -427,31 +458,31 @@ bfly_status run(bfly_plan_t P, const void *in, void *out, int nrhs, int dtype, b
   if (n_in == 0 || n_out == 0) {
     BFLY_CUDA(mark());
     if (n_out > 0) BFLY_CUDA(cudaMemsetAsync(out, 0, (size_t)nrhs * n_out * (io64 ? 16 : 8), s));
-    while (ev && n < L + 3) BFLY_CUDA(mark());
+    while (ev && n < S + 3) BFLY_CUDA(mark());
     return BFLY_OK;
   }
   if (!adjoint) {
     // step 2: leaf charges (stage L) from the sources
     BFLY_CUDA(mark());
-    BFLY_CUDA(P->ks->spread(point_args(P, false, in, P->buf[L & 1], nrhs, io64, false,
+    BFLY_CUDA(P->ks->spread(point_args(P, false, in, P->buf[0], nrhs, io64, false,
                                        P->pairs[L] * PD), s));
-    // step 3: stages L-1 .. 0
-    for (int t = L - 1; t >= 0; --t) {
+    // step 3: stages L-1 .. 0, one or two per launch
+    for (int si = 0; si < S; ++si) {
       BFLY_CUDA(mark());
-      BFLY_CUDA(P->ks->level(level_args(P, t, false, nrhs), false, P->level_grid, P->level_smem, s));
+      BFLY_CUDA(P->ks->level(level_args(P, si, false, nrhs), false, P->level_grid, P->level_smem, s));
     }
     // step 4: evaluate at the targets from stage 0
     BFLY_CUDA(mark());
-    BFLY_CUDA(P->ks->interp(point_args(P, true, P->buf[0], out, nrhs, io64, false, P->pairs[0] * PD), s));
+    BFLY_CUDA(P->ks->interp(point_args(P, true, P->buf[S & 1], out, nrhs, io64, false, P->pairs[0] * PD), s));
   } else {
     BFLY_CUDA(mark());
-    BFLY_CUDA(P->ks->spread(point_args(P, true, in, P->buf[0], nrhs, io64, true, P->pairs[0] * PD), s));
-    for (int t = 0; t < L; ++t) {
+    BFLY_CUDA(P->ks->spread(point_args(P, true, in, P->buf[S & 1], nrhs, io64, true, P->pairs[0] * PD), s));
+    for (int si = S - 1; si >= 0; --si) {
       BFLY_CUDA(mark());
-      BFLY_CUDA(P->ks->level(level_args(P, t, true, nrhs), true, P->level_grid, P->level_smem, s));
+      BFLY_CUDA(P->ks->level(level_args(P, si, true, nrhs), true, P->level_grid, P->level_smem, s));
     }
     BFLY_CUDA(mark());
-    BFLY_CUDA(P->ks->interp(point_args(P, false, P->buf[L & 1], out, nrhs, io64, true,
+    BFLY_CUDA(P->ks->interp(point_args(P, false, P->buf[0], out, nrhs, io64, true,
                                        P->pairs[L] * PD), s));
   }
   BFLY_CUDA(mark());
@@ -500,7 +531,8 @@ bfly_status bfly_execute_events(bfly_plan_t plan, const void *in, void *out, int
   g_err.clear();
   bfly_status st = check_exec(plan, in, out, nrhs, dtype, adjoint != 0);
   if (st != BFLY_OK) return st;
-  if (!events || n_events != plan->L + 3) return fail(BFLY_ERR_INVALID_ARG, "events must hold L + 3 entries");
+  if (!events || n_events != (int)plan->steps.size() + 3)
+    return fail(BFLY_ERR_INVALID_ARG, "events must hold steps + 3 entries (bfly_plan_info_t.steps)");
   return run(plan, in, out, nrhs, dtype, adjoint != 0, reinterpret_cast<cudaStream_t>(stream),
              reinterpret_cast<cudaEvent_t const *>(events));
 }

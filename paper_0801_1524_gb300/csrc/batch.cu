@@ -1,8 +1,9 @@
 // Batched execution of many plans (independent transforms of uneven N and point counts,
 // each with nrhs right-hand sides; the plans share dim, p, precision and tile capacities,
 // and so the operators): the leaf step of every plan, then one launch of the
-// recursive-step kernel per stage t = L_max-1 .. 0 over the chunks of every plan that
-// has that stage (plans are aligned at the final stage), then the final step of every
+// recursive-step kernel per stage t = L_max-1 .. 0 over the chunks of every plan's step
+// that starts at stage t (one or two stages; plans are aligned at the final stage), then
+// the final step of every
 // plan.  On a non-default stream the whole sequence is captured once into a CUDA graph
 // and replayed while the buffers and nrhs stay the same.
 #include <algorithm>
@@ -53,10 +54,11 @@ bfly_status launch_all(bfly_batch_t B, const void *const *f, void *const *u, int
       if (P->nx > 0) BATCH_CUDA(cudaMemsetAsync(u[i], 0, (size_t)nrhs * P->nx * (io64 ? 16 : 8), s));
       continue;
     }
-    BATCH_CUDA(P->ks->spread(point_args(P, false, f[i], P->buf[P->L & 1], nrhs, io64, false,
+    BATCH_CUDA(P->ks->spread(point_args(P, false, f[i], P->buf[0], nrhs, io64, false,
                                         P->pairs[P->L] * P->TS), s));
   }
   bfly_plan_t P0 = B->plans[0];
+  // launch t: the steps of every plan that start at stage t (one or two stages each)
   for (int t = B->L_max - 1; t >= 0; --t) {
     if (B->n_entries[t] == 0) continue;
     // the operators and tile capacities of plan 0 serve all (same dim, p, precision)
@@ -76,7 +78,7 @@ bfly_status launch_all(bfly_batch_t B, const void *const *f, void *const *u, int
   for (int i = 0; i < B->count; ++i) {
     bfly_plan_t P = B->plans[i];
     if (empty(P)) continue;
-    BATCH_CUDA(P->ks->interp(point_args(P, true, P->buf[0], u[i], nrhs, io64, false,
+    BATCH_CUDA(P->ks->interp(point_args(P, true, P->buf[P->steps.size() & 1], u[i], nrhs, io64, false,
                                         P->pairs[0] * P->TS), s));
   }
   return BFLY_OK;
@@ -138,18 +140,21 @@ bfly_status bfly_batch_create(bfly_batch_t *out, int count, const bfly_plan_t *p
   for (int t = 0; t < B->L_max; ++t) {
     std::vector<double> work;  // the chunks of every plan, scheduled together
     for (auto *P : B->plans) {
-      if (t >= P->L) continue;
-      const bfly::StageProgram &pg = P->progF[t];
+      int si = 0;
+      while (si < (int)P->steps.size() && P->steps[si].t != t) ++si;
+      if (si == (int)P->steps.size()) continue;  // no step of this plan starts at stage t
+      const int t_lo = t - P->steps[si].levels + 1;
+      const bfly::StageProgram &pg = P->progF[si];
       for (const bfly::ChunkDesc &cd : pg.chunks) {
         work.push_back(bfly::chunk_work(pg.blob.data() + cd.blob_off, B->dim, B->p));
         bfly::BatchEntry e;
         e.d = cd;
-        e.blob = P->dF[t].blob;
-        e.runs = P->dF[t].runs;
-        e.in = P->buf[(t + 1) & 1];
-        e.out = P->buf[t & 1];
+        e.blob = P->dF[si].blob;
+        e.runs = P->dF[si].runs;
+        e.in = P->buf[si & 1];
+        e.out = P->buf[(si + 1) & 1];
         e.in_rhs = P->pairs[t + 1] * P->TS;
-        e.out_rhs = P->pairs[t] * P->TS;
+        e.out_rhs = P->pairs[t_lo] * P->TS;
         host[t].push_back(e);
       }
     }

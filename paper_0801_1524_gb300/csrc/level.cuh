@@ -1,13 +1,16 @@
-// Recursive step of the butterfly (Sec. 2.2 step 3, Fig. 1), one launch per stage.
+// Recursive step of the butterfly (Sec. 2.2 step 3, Fig. 1), one launch per step of one
+// stage or (2D) two consecutive stages.
 //
 // For every pair (A, B) at stage t the charges are
 //     f^{AB} = sum_{c in children(B)} ( (x)_d T^{(alpha_d(A), delta_d(c))} ) f^{A' Bc}
 // with A' the parent of A and T the per-axis transfer operators (plan.cpp).  The host
-// compiles every stage into chunks of units (A', B) with one item list per axis: pass k
-// applies the operator of axis k to at most two source tiles and sums them (the sources
-// agree on every bit still to be applied; sum factorisation):
-//   inputs --pass 0--> scratch --pass 1 (3D)--> input slot --last pass--> global.
-// The adjoint sweep runs the same kernel on the adjoint program with the
+// compiles every step into chunks of units with one item list per pass: pass j applies
+// the operator of axis j mod D to at most two source tiles and sums them (the sources
+// agree on every bit still to be applied; sum factorisation).  The passes alternate
+// between the slot's input buffer and the scratch buffer,
+//   inputs --pass 0--> scratch --pass 1--> input slot --pass 2--> scratch ...,
+// and the last pass's tiles are written back; in a two-stage step the tiles of the stage
+// between the two levels never leave shared memory.  The adjoint sweep runs the same kernel on the adjoint program with the
 // conjugate-transposed operators.  A batched launch runs the chunks of many plans (same
 // dim, p and precision): a per-chunk entry then names the chunk's buffers.
 //
@@ -60,12 +63,14 @@ struct LevelShape {
   static constexpr size_t table_bytes = (size_t)NOPS * P * P * sizeof(C);  // as C^{(gamma,delta)}
   static constexpr size_t tile_bytes = (size_t)TS * sizeof(C);
   static int meta_bytes(int cap0, int cap1, int max_out) {
-    // header, an item (8 bytes) per pass tile, one run (8 bytes) per output, padding
-    const int items = cap1 + (D == 3 ? cap0 : 0) + max_out;
+    // header, an item (8 bytes) per pass tile, one run (8 bytes) per output, padding.  In
+    // 2D a step has up to two levels (passes into scratch, input, scratch buffers and the
+    // staged outputs); in 3D one (scratch, input, staged outputs)
+    const int items = (D == 2 ? 2 * cap1 + cap0 : cap1 + cap0) + max_out;
     return (kBlobHeader + 8 * items + 8 * max_out + 15) & ~15;
   }
-  // 4 mbarriers | 2 metadata slots | 2 input buffers | scratch (2 in 3D, where the last
-  // pass stages its outputs there)
+  // 4 mbarriers | 2 metadata slots | 2 input buffers | scratch (2 in 3D, where a
+  // one-level step stages its outputs there)
   static constexpr int NSCR = D == 3 ? 2 : 1;
   static size_t bytes(const ChunkCaps &c) {
     size_t b = 64;
@@ -372,9 +377,12 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
     auto write_back = [&](int s, long long w) {
       const unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
       const int32_t *hdr = reinterpret_cast<const int32_t *>(meta_s);
-      const int n_items = hdr[0] + hdr[1] + hdr[2], n_oruns = hdr[7];
+      const int NP = hdr[0], n_oruns = hdr[2];
+      int n_items = 0;
+      for (int j = 0; j < NP; ++j) n_items += hdr[4 + j];
       const Run *oruns = reinterpret_cast<const Run *>(meta_s + kBlobHeader + (size_t)n_items * sizeof(Item));
-      const C *stage_t = D == 3 ? scr0 + (size_t)(s % S::NSCR) * a.cap1 * TS : slot0 + (size_t)s * a.cap0 * TS;
+      // the last pass wrote the input buffer (odd pass) or the scratch buffer (even)
+      const C *stage_t = ((NP - 1) & 1) ? slot0 + (size_t)s * a.cap0 * TS : scr0 + (size_t)(s % S::NSCR) * a.cap1 * TS;
       const unsigned char *stage = reinterpret_cast<const unsigned char *>(stage_t);
       unsigned char *obase = gout;
       int64_t orhs = a.out_rhs;
@@ -490,16 +498,25 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
     C *in_s = slot0 + (size_t)s * a.cap0 * TS;
     C *scr = scr0 + (size_t)(s % S::NSCR) * a.cap1 * TS;
     const int32_t *hdr = reinterpret_cast<const int32_t *>(meta_s);
-    const Item *i0 = reinterpret_cast<const Item *>(meta_s + kBlobHeader);
-    const Item *i1 = i0 + hdr[0];
-    run_pass<R, D, P, 0, ADJ>(i0, hdr[0], hdr[3], in_s, scr, warp, lane);
-    consumer_sync();
-    if (D == 3) {
-      run_pass<R, D, P, (D == 3 ? 1 : 0), ADJ>(i1, hdr[1], hdr[4], scr, in_s, warp, lane);
+    const int NP = hdr[0];
+    const Item *ip = reinterpret_cast<const Item *>(meta_s + kBlobHeader);
+    // pass j (axis j mod D) reads the buffer pass j-1 wrote and writes the scratch buffer
+    // (even j) or the input buffer (odd j); a barrier between passes
+    for (int j = 0; j < NP; j += D) {
+      if (j > 0) consumer_sync();
+      run_pass<R, D, P, 0, ADJ>(ip, hdr[4 + j], hdr[4 + kMaxPasses + j], (j & 1) ? scr : in_s,
+                                (j & 1) ? in_s : scr, warp, lane);
+      ip += hdr[4 + j];
       consumer_sync();
-      run_pass<R, D, P, D - 1, ADJ>(i1 + hdr[1], hdr[2], hdr[5], in_s, scr, warp, lane);  // staged in scr
-    } else {
-      run_pass<R, D, P, D - 1, ADJ>(i1, hdr[1], hdr[4], scr, in_s, warp, lane);  // staged in in_s
+      run_pass<R, D, P, 1, ADJ>(ip, hdr[5 + j], hdr[5 + kMaxPasses + j], (j & 1) ? in_s : scr,
+                                (j & 1) ? scr : in_s, warp, lane);
+      ip += hdr[5 + j];
+      if constexpr (D == 3) {
+        consumer_sync();
+        run_pass<R, D, P, (D == 3 ? 2 : 0), ADJ>(ip, hdr[6 + j], hdr[6 + kMaxPasses + j], (j & 1) ? scr : in_s,
+                                                 (j & 1) ? in_s : scr, warp, lane);
+        ip += hdr[6 + j];
+      }
     }
     fence_async_shared();  // the staged tiles are visible to the bulk stores
     consumer_sync();

@@ -92,15 +92,16 @@ extern "C" bfly_status bfly_execute_noalloc(bfly_plan_t plan, const void *f, voi
     NOALLOC_CUDA(cudaMemsetAsync(u, 0, (size_t)nrhs * plan->nx * (io64 ? 16 : 8), s));
     return BFLY_OK;
   }
-  const int L = plan->L, TS = plan->TS;
-  NOALLOC_CUDA(plan->ks->spread(point_args(plan, false, f, buf[L & 1], nrhs, io64, false,
+  const int L = plan->L, TS = plan->TS, S = (int)plan->steps.size();
+  // boundary b of the sweep (b = 0: stage L, b = S: stage 0) in buf[b mod 2]
+  NOALLOC_CUDA(plan->ks->spread(point_args(plan, false, f, buf[0], nrhs, io64, false,
                                            plan->pairs[L] * TS), s));
-  for (int t = L - 1; t >= 0; --t) {
-    bfly::LevelArgs a = level_args(plan, t, false, nrhs);
-    a.in = buf[(t + 1) & 1];
-    a.out = buf[t & 1];
+  for (int si = 0; si < S; ++si) {
+    bfly::LevelArgs a = level_args(plan, si, false, nrhs);
+    a.in = buf[si & 1];
+    a.out = buf[(si + 1) & 1];
     NOALLOC_CUDA(plan->ks->level(a, false, plan->level_grid, plan->level_smem, s));
   }
-  NOALLOC_CUDA(plan->ks->interp(point_args(plan, true, buf[0], u, nrhs, io64, false, plan->pairs[0] * TS), s));
+  NOALLOC_CUDA(plan->ks->interp(point_args(plan, true, buf[S & 1], u, nrhs, io64, false, plan->pairs[0] * TS), s));
   return BFLY_OK;
 }

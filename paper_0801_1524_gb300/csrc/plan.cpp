@@ -172,41 +172,139 @@ struct UnitProg {
   int32_t out_tile[8];
 };
 
-}  // namespace
-
-StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp,
-                                const std::vector<int32_t> &xidx, const std::vector<int32_t> &csB,
-                                const std::vector<int32_t> &kidx, bool adjoint, ChunkCaps caps) {
-  StageProgram prog;
-  const int D = dim;
-  const int64_t nAp = (int64_t)csAp.size() - 1, nB = (int64_t)csB.size() - 1;
-  const int64_t nBc = (int64_t)kidx.size() / dim;
+// The unit (A', B) = (iAp, iB) of one stage (trees S).
+UnitProg build_unit(int D, const StageTrees &S, int64_t iAp, int64_t iB, bool adjoint) {
+  const std::vector<int32_t> &csAp = *S.csAp, &xidx = *S.xidx, &csB = *S.csB, &kidx = *S.kidx;
+  const int64_t nB = (int64_t)csB.size() - 1, nBc = (int64_t)kidx.size() / D;
   const int64_t in_row = adjoint ? nB : nBc, out_row = adjoint ? nBc : nB;
   auto lo = [](int k) { return (1 << (k + 1)) - 1; };     // bits 0..k
   auto hi = [&](int k) { return ((1 << D) - 1) & ~lo(k); };  // bits k+1..D-1
+  const int a0 = csAp[iAp], a1 = csAp[iAp + 1];
+  const int c0 = csB[iB], c1 = csB[iB + 1];
+  UnitProg U;
+  int gam[8], ng = 0, del[8], nd = 0;
+  int32_t gtile[8], dtile[8];
+  for (int a = a0; a < a1; ++a) {
+    int g = 0;
+    for (int d = 0; d < D; ++d) g |= (xidx[(int64_t)a * D + d] & 1) << d;
+    gam[ng] = g;
+    gtile[ng++] = a;
+  }
+  for (int c = c0; c < c1; ++c) {
+    int dl = 0;
+    for (int d = 0; d < D; ++d) dl |= (kidx[(int64_t)c * D + d] & 1) << d;
+    del[nd] = dl;
+    dtile[nd++] = c;
+  }
+  // inputs and outputs with their keys and global tiles
+  const int n_in = adjoint ? ng : nd, n_out = adjoint ? nd : ng;
+  const int *ikey = adjoint ? gam : del, *okey = adjoint ? del : gam;
+  U.n_in = n_in;
+  for (int i = 0; i < n_in; ++i) {
+    U.in_key[i] = ikey[i];
+    U.in_tile[i] = adjoint ? (int32_t)((int64_t)gtile[i] * in_row + iB) : (int32_t)(iAp * in_row + dtile[i]);
+  }
+  for (int k = 0; k < D; ++k) {
+    // needed keys of pass k: out-prefix (bits 0..k) x in-suffix (bits k+1..)
+    int nk2 = 0;
+    for (int o = 0; o < n_out; ++o)
+      for (int i = 0; i < n_in; ++i) {
+        const int K = (okey[o] & lo(k)) | (ikey[i] & hi(k));
+        bool seen = false;
+        for (int j = 0; j < nk2; ++j) seen |= U.key[k][j] == K;
+        if (!seen) U.key[k][nk2++] = K;
+      }
+    U.n_pass[k] = nk2;
+    for (int v = 0; v < nk2; ++v) {
+      const int K = U.key[k][v];
+      const int obit = (K >> k) & 1;
+      for (int b = 0; b < 2; ++b) {
+        const int Sk = (K & ~(1 << k)) | (b << k);
+        int found = -1;
+        if (k == 0) {
+          for (int i = 0; i < n_in; ++i)
+            if (U.in_key[i] == Sk) found = i;  // input keys are all in-side bits
+        } else {
+          for (int j = 0; j < U.n_pass[k - 1]; ++j)
+            if (U.key[k - 1][j] == Sk) found = j;
+        }
+        U.src[k][v][b] = found;
+        // operator gamma*2 + delta: forward, gamma is the output (A) bit and delta = b;
+        // adjoint, gamma is the input (A) bit b and delta the output (Bc) bit
+        U.op[k][v][b] = adjoint ? b * 2 + obit : obit * 2 + b;
+      }
+    }
+  }
+  for (int v = 0; v < U.n_pass[D - 1]; ++v) {
+    // the last pass's keys are output keys: find that output's tile
+    for (int o = 0; o < n_out; ++o)
+      if (okey[o] == U.key[D - 1][v])
+        U.out_tile[v] = adjoint ? (int32_t)(iAp * out_row + dtile[o]) : (int32_t)((int64_t)gtile[o] * out_row + iB);
+  }
+  return U;
+}
 
-  int tot_in = 0, tot[3] = {0, 0, 0};
-  std::vector<UnitProg> units;
+// A unit of a step: its subunits level by level (one level: a single unit).
+struct StepUnit {
+  std::vector<UnitProg> lev[2];
+};
+
+}  // namespace
+
+StageProgram make_step_program(int dim, int p, const StageTrees *st, int levels, bool adjoint, ChunkCaps caps,
+                               bool *fits) {
+  StageProgram prog;
+  const int D = dim, NL = levels, NP = levels * dim;
+  if (fits) *fits = true;
+  // running totals of the chunk being filled: inputs and the outputs of every pass
+  struct Tot {
+    int in = 0, pass[kMaxPasses] = {0, 0, 0, 0, 0, 0};
+  };
+  auto add = [&](Tot &t, const StepUnit &m) {
+    for (const UnitProg &u : m.lev[0]) t.in += u.n_in;
+    for (int l = 0; l < NL; ++l)
+      for (const UnitProg &u : m.lev[l])
+        for (int k = 0; k < D; ++k) t.pass[l * D + k] += u.n_pass[k];
+  };
+  // pass j writes the scratch buffer (even j) or the input buffer (odd j); the last
+  // pass's outputs are staged there and written back as runs
+  auto within = [&](const Tot &t) {
+    int need0 = t.in, need1 = 0, items = 0;
+    for (int j = 0; j < NP; ++j) {
+      if (j & 1) need0 = std::max(need0, t.pass[j]);
+      else need1 = std::max(need1, t.pass[j]);
+      items += t.pass[j];
+    }
+    const int nout = t.pass[NP - 1];
+    const int meta = kBlobHeader + 8 * items + 8 * nout + 15;
+    return need0 <= caps.cap0 && need1 <= caps.cap1 && nout <= caps.max_out && meta <= caps.meta_bytes;
+  };
+
+  std::vector<StepUnit> cur;
+  Tot tot;
   auto flush = [&]() {
-    if (units.empty()) return;
-    ChunkDesc cur{};
-    cur.n_in = tot_in;
-    for (int k = 0; k < 3; ++k) cur.n_item[k] = k < D ? tot[k] : 0;
+    if (cur.empty()) return;
+    ChunkDesc cd{};
+    std::vector<const UnitProg *> su[2];
+    for (const StepUnit &m : cur)
+      for (int l = 0; l < NL; ++l)
+        for (const UnitProg &u : m.lev[l]) su[l].push_back(&u);
     // inputs of the chunk in global order: slot = rank, so that runs are contiguous
     std::vector<std::pair<int32_t, int>> order;  // (global tile, unit-local key index)
-    std::vector<int> base_in(units.size());
+    std::vector<int> base_in(su[0].size());
     int bi = 0;
-    for (size_t u = 0; u < units.size(); ++u) {
+    for (size_t u = 0; u < su[0].size(); ++u) {
       base_in[u] = bi;
-      for (int i = 0; i < units[u].n_in; ++i) order.push_back({units[u].in_tile[i], bi + i});
-      bi += units[u].n_in;
+      for (int i = 0; i < su[0][u]->n_in; ++i) order.push_back({su[0][u]->in_tile[i], bi + i});
+      bi += su[0][u]->n_in;
     }
+    cd.n_in = bi;
     std::vector<std::pair<int32_t, int>> sorted = order;
     std::sort(sorted.begin(), sorted.end());
     std::vector<int> slot_of(order.size());
     for (size_t r = 0; r < sorted.size(); ++r) slot_of[sorted[r].second] = (int)r;
     prog.in_off.push_back((int32_t)prog.in_tiles.size());
-    cur.run_off = (int32_t)prog.runs.size();
+    cd.run_off = (int32_t)prog.runs.size();
     for (size_t r = 0; r < sorted.size(); ++r) {
       prog.in_tiles.push_back(sorted[r].first);
       if (r > 0 && sorted[r].first == sorted[r - 1].first + 1 && prog.runs.back().count < 0xffff)
@@ -214,65 +312,85 @@ StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp
       else
         prog.runs.push_back(Run{sorted[r].first, (uint16_t)r, 1});
     }
-    cur.n_runs = (int32_t)prog.runs.size() - cur.run_off;
-    // pass tiles numbered unit by unit
-    std::vector<int> base[3];
-    for (int k = 0; k < 3; ++k) base[k].resize(units.size());
-    int bk[3] = {0, 0, 0};
-    for (size_t u = 0; u < units.size(); ++u)
+    cd.n_runs = (int32_t)prog.runs.size() - cd.run_off;
+    // output slots of every pass, numbered subunit by subunit
+    std::vector<int> base[2][3];
+    for (int l = 0; l < NL; ++l)
       for (int k = 0; k < D; ++k) {
-        base[k][u] = bk[k];
-        bk[k] += units[u].n_pass[k];
-      }
-    // items pass by pass; the last pass's destination is the staging slot of its output,
-    // numbered in global order so that outputs form contiguous runs
-    std::vector<int32_t> outs;
-    for (size_t u = 0; u < units.size(); ++u)
-      for (int v = 0; v < units[u].n_pass[D - 1]; ++v) outs.push_back(units[u].out_tile[v]);
-    std::vector<int32_t> osorted = outs;
-    std::sort(osorted.begin(), osorted.end());
-    std::vector<Item> items;
-    int32_t icount[3] = {0, 0, 0}, tcount[3] = {0, 0, 0};
-    int oi = 0;
-    for (int k = 0; k < D; ++k) {
-      std::vector<Item> pass;
-      for (size_t u = 0; u < units.size(); ++u) {
-        const UnitProg &U = units[u];
-        for (int v = 0; v < U.n_pass[k]; ++v) {
-          Item e{0xffff, 0xffff, 0, 0};
-          if (k == D - 1) {
-            const int32_t g = outs[oi++];
-            e.dst = (uint16_t)(std::lower_bound(osorted.begin(), osorted.end(), g) - osorted.begin());
-          } else {
-            e.dst = (uint16_t)(base[k][u] + v);
-          }
-          int got = 0;
-          for (int j = 0; j < 2; ++j) {
-            const int sidx = U.src[k][v][j];
-            if (sidx < 0) continue;
-            const uint16_t slot = (uint16_t)(k == 0 ? slot_of[base_in[u] + sidx] : base[k - 1][u] + sidx);
-            if (got == 0) {
-              e.src0 = slot;
-              e.ops = (uint16_t)U.op[k][v][j];
-            } else {
-              e.src1 = slot;
-              e.ops |= (uint16_t)(U.op[k][v][j] << 2);
-            }
-            ++got;
-          }
-          pass.push_back(e);
+        base[l][k].resize(su[l].size());
+        int b = 0;
+        for (size_t u = 0; u < su[l].size(); ++u) {
+          base[l][k][u] = b;
+          b += su[l][u]->n_pass[k];
         }
       }
-      // two-source items first, then by the delta and gamma of the first operator: a
-      // step then rarely mixes one- and two-source fibres or operators of both deltas
-      std::stable_sort(pass.begin(), pass.end(), [](const Item &x, const Item &y) {
-        const int kx = ((x.src1 == 0xffff) << 2) | ((x.ops & 1) << 1) | ((x.ops >> 1) & 1);
-        const int ky = ((y.src1 == 0xffff) << 2) | ((y.ops & 1) << 1) | ((y.ops >> 1) & 1);
-        return kx < ky;
-      });
-      icount[k] = (int32_t)pass.size();
-      for (const Item &e : pass) tcount[k] += e.src1 != 0xffff;
-      items.insert(items.end(), pass.begin(), pass.end());
+    // the last level's outputs: staging slots in global order, so that they form runs
+    std::vector<int32_t> outs;
+    for (const UnitProg *u : su[NL - 1])
+      for (int v = 0; v < u->n_pass[D - 1]; ++v) outs.push_back(u->out_tile[v]);
+    std::vector<int32_t> osorted = outs;
+    std::sort(osorted.begin(), osorted.end());
+    std::vector<std::pair<int32_t, int>> inter;  // (global tile, slot) of the previous level's outputs
+    std::vector<Item> items;
+    int32_t icount[kMaxPasses] = {0}, tcount[kMaxPasses] = {0};
+    for (int l = 0; l < NL; ++l) {
+      std::vector<std::pair<int32_t, int>> next_inter;
+      for (int k = 0; k < D; ++k) {
+        const int j = l * D + k;
+        std::vector<Item> pass;
+        for (size_t u = 0; u < su[l].size(); ++u) {
+          const UnitProg &U = *su[l][u];
+          for (int v = 0; v < U.n_pass[k]; ++v) {
+            Item e{0xffff, 0xffff, 0, 0};
+            if (k < D - 1 || l < NL - 1) {
+              e.dst = (uint16_t)(base[l][k][u] + v);
+              if (k == D - 1) next_inter.push_back({U.out_tile[v], base[l][k][u] + v});
+            } else {
+              e.dst = (uint16_t)(std::lower_bound(osorted.begin(), osorted.end(), U.out_tile[v]) - osorted.begin());
+            }
+            int got = 0;
+            for (int b = 0; b < 2; ++b) {
+              const int sidx = U.src[k][v][b];
+              if (sidx < 0) continue;
+              int slot;
+              if (k > 0) {
+                slot = base[l][k - 1][u] + sidx;
+              } else if (l == 0) {
+                slot = slot_of[base_in[u] + sidx];
+              } else {
+                // an intermediate tile of the previous level, by its global index
+                const auto it = std::lower_bound(inter.begin(), inter.end(), std::make_pair(U.in_tile[sidx], -1));
+                slot = it != inter.end() && it->first == U.in_tile[sidx] ? it->second : -1;
+                if (slot < 0) {  // not produced in this chunk: cannot happen for whole units
+                  if (fits) *fits = false;
+                  slot = 0;
+                }
+              }
+              if (got == 0) {
+                e.src0 = (uint16_t)slot;
+                e.ops = (uint16_t)U.op[k][v][b];
+              } else {
+                e.src1 = (uint16_t)slot;
+                e.ops |= (uint16_t)(U.op[k][v][b] << 2);
+              }
+              ++got;
+            }
+            pass.push_back(e);
+          }
+        }
+        // two-source items first, then by the delta and gamma of the first operator: a
+        // step then rarely mixes one- and two-source fibres or operators of both deltas
+        std::stable_sort(pass.begin(), pass.end(), [](const Item &x, const Item &y) {
+          const int kx = ((x.src1 == 0xffff) << 2) | ((x.ops & 1) << 1) | ((x.ops >> 1) & 1);
+          const int ky = ((y.src1 == 0xffff) << 2) | ((y.ops & 1) << 1) | ((y.ops >> 1) & 1);
+          return kx < ky;
+        });
+        icount[j] = (int32_t)pass.size();
+        for (const Item &e : pass) tcount[j] += e.src1 != 0xffff;
+        items.insert(items.end(), pass.begin(), pass.end());
+      }
+      std::sort(next_inter.begin(), next_inter.end());
+      inter.swap(next_inter);
     }
     std::vector<Run> oruns;
     for (size_t r = 0; r < osorted.size(); ++r) {
@@ -281,104 +399,68 @@ StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp
       else
         oruns.push_back(Run{osorted[r], (uint16_t)r, 1});
     }
-    cur.blob_off = (int32_t)prog.blob.size();
-    const int32_t header[kBlobHeader / 4] = {icount[0], icount[1], icount[2], tcount[0],
-                                             tcount[1], tcount[2], cur.n_in, (int32_t)oruns.size()};
+    cd.blob_off = (int32_t)prog.blob.size();
+    cd.n_pass = NP;
+    int32_t header[kBlobHeader / 4] = {0};
+    header[0] = NP;
+    header[1] = cd.n_in;
+    header[2] = (int32_t)oruns.size();
+    for (int j = 0; j < NP; ++j) {
+      header[4 + j] = icount[j];
+      header[4 + kMaxPasses + j] = tcount[j];
+    }
     const size_t ib = items.size() * sizeof(Item), ob = oruns.size() * sizeof(Run);
     const size_t bytes = (kBlobHeader + ib + ob + 15) & ~(size_t)15;
     prog.blob.resize(prog.blob.size() + bytes, 0);
-    unsigned char *dstp = prog.blob.data() + cur.blob_off;
+    unsigned char *dstp = prog.blob.data() + cd.blob_off;
     std::memcpy(dstp, header, kBlobHeader);
     std::memcpy(dstp + kBlobHeader, items.data(), ib);
     std::memcpy(dstp + kBlobHeader + ib, oruns.data(), ob);
-    cur.blob_bytes = (int32_t)bytes;
-    prog.chunks.push_back(cur);
-    units.clear();
-    tot_in = 0;
-    tot[0] = tot[1] = tot[2] = 0;
+    cd.blob_bytes = (int32_t)bytes;
+    prog.chunks.push_back(cd);
+    cur.clear();
+    tot = Tot();
+  };
+  auto push = [&](StepUnit &&m) {
+    Tot t2 = tot;
+    add(t2, m);
+    if (!cur.empty() && !within(t2)) {
+      flush();
+      t2 = Tot();
+      add(t2, m);
+    }
+    if (!within(t2) && fits) *fits = false;  // a unit alone exceeds the capacities
+    cur.push_back(std::move(m));
+    tot = t2;
   };
 
-  for (int64_t iAp = 0; iAp < nAp; ++iAp) {
-    const int a0 = csAp[iAp], a1 = csAp[iAp + 1];
-    int apar[3] = {0, 0, 0};
-    for (int d = 0; d < D; ++d) apar[d] = xidx[(int64_t)a0 * D + d] >> 1;
-    for (int64_t iB = 0; iB < nB; ++iB) {
-      const int c0 = csB[iB], c1 = csB[iB + 1];
-      UnitProg U;
-      int gam[8], ng = 0, del[8], nd = 0;
-      int32_t gtile[8], dtile[8];
-      for (int a = a0; a < a1; ++a) {
-        int g = 0;
-        for (int d = 0; d < D; ++d) g |= (xidx[(int64_t)a * D + d] & 1) << d;
-        gam[ng] = g;
-        gtile[ng++] = a;
+  if (NL == 1) {
+    const StageTrees &S = st[0];
+    const int64_t nAp = (int64_t)S.csAp->size() - 1, nB = (int64_t)S.csB->size() - 1;
+    for (int64_t iAp = 0; iAp < nAp; ++iAp)
+      for (int64_t iB = 0; iB < nB; ++iB) {
+        StepUnit m;
+        m.lev[0].push_back(build_unit(D, S, iAp, iB, adjoint));
+        push(std::move(m));
       }
-      for (int c = c0; c < c1; ++c) {
-        int dl = 0;
-        for (int d = 0; d < D; ++d) dl |= (kidx[(int64_t)c * D + d] & 1) << d;
-        del[nd] = dl;
-        dtile[nd++] = c;
+  } else {
+    // stages t (trees st[0]) and t-1 (st[1]): unit (A'', B_) with A'' a box of the A'
+    // level of stage t and B_ one of the B level of stage t-1.  Its stage-t units are
+    // (A'', B) for the children B of B_, its stage-(t-1) units (A, B_) for the children
+    // A of A''; the stage-t tiles f^{A B} between them stay in shared memory.
+    const StageTrees &Shi = st[0], &Slo = st[1];
+    const int64_t nA2 = (int64_t)Shi.csAp->size() - 1, nB2 = (int64_t)Slo.csB->size() - 1;
+    for (int64_t iA2 = 0; iA2 < nA2; ++iA2)
+      for (int64_t iB2 = 0; iB2 < nB2; ++iB2) {
+        StepUnit m;
+        std::vector<UnitProg> hiU, loU;
+        for (int32_t b = (*Slo.csB)[iB2]; b < (*Slo.csB)[iB2 + 1]; ++b) hiU.push_back(build_unit(D, Shi, iA2, b, adjoint));
+        for (int32_t a = (*Shi.csAp)[iA2]; a < (*Shi.csAp)[iA2 + 1]; ++a) loU.push_back(build_unit(D, Slo, a, iB2, adjoint));
+        // forward: stage t first; adjoint: the adjoint of stage t-1 first
+        m.lev[0] = adjoint ? std::move(loU) : std::move(hiU);
+        m.lev[1] = adjoint ? std::move(hiU) : std::move(loU);
+        push(std::move(m));
       }
-      // inputs and outputs with their keys and global tiles
-      const int n_in = adjoint ? ng : nd, n_out = adjoint ? nd : ng;
-      const int *ikey = adjoint ? gam : del, *okey = adjoint ? del : gam;
-      U.n_in = n_in;
-      for (int i = 0; i < n_in; ++i) {
-        U.in_key[i] = ikey[i];
-        U.in_tile[i] = adjoint ? (int32_t)((int64_t)gtile[i] * in_row + iB)
-                               : (int32_t)(iAp * in_row + dtile[i]);
-      }
-      for (int k = 0; k < D; ++k) {
-        // needed keys of pass k: out-prefix (bits 0..k) x in-suffix (bits k+1..)
-        int nk2 = 0;
-        for (int o = 0; o < n_out; ++o)
-          for (int i = 0; i < n_in; ++i) {
-            const int K = (okey[o] & lo(k)) | (ikey[i] & hi(k));
-            bool seen = false;
-            for (int j = 0; j < nk2; ++j) seen |= U.key[k][j] == K;
-            if (!seen) U.key[k][nk2++] = K;
-          }
-        U.n_pass[k] = nk2;
-        for (int v = 0; v < nk2; ++v) {
-          const int K = U.key[k][v];
-          const int obit = (K >> k) & 1;
-          for (int b = 0; b < 2; ++b) {
-            const int S = (K & ~(1 << k)) | (b << k);
-            int found = -1;
-            if (k == 0) {
-              for (int i = 0; i < n_in; ++i)
-                if (U.in_key[i] == S) found = i;  // input keys are all in-side bits
-            } else {
-              for (int j = 0; j < U.n_pass[k - 1]; ++j)
-                if (U.key[k - 1][j] == S) found = j;
-            }
-            U.src[k][v][b] = found;
-            // operator gamma*2 + delta: forward, gamma is the output (A) bit and delta = b;
-            // adjoint, gamma is the input (A) bit b and delta the output (Bc) bit
-            U.op[k][v][b] = adjoint ? b * 2 + obit : obit * 2 + b;
-          }
-        }
-      }
-      for (int v = 0; v < U.n_pass[D - 1]; ++v) {
-        // the last pass's keys are output keys: find that output's tile
-        for (int o = 0; o < n_out; ++o)
-          if (okey[o] == U.key[D - 1][v])
-            U.out_tile[v] = adjoint ? (int32_t)(iAp * out_row + dtile[o])
-                                    : (int32_t)((int64_t)gtile[o] * out_row + iB);
-      }
-      // capacity: buffer 0 holds inputs (and pass 1 in 3D), buffer 1 pass 0
-      const int need0 = std::max(tot_in + U.n_in, D == 3 ? tot[1] + U.n_pass[1] : 0);
-      const int need1 = tot[0] + U.n_pass[0];
-      const int needo = tot[D - 1] + U.n_pass[D - 1];
-      // header, an item per pass tile, one run per output, padding
-      const int needb = kBlobHeader + 8 * (need1 + (D == 3 ? tot[1] + U.n_pass[1] : 0) + needo) + 8 * needo + 15;
-      if (!units.empty() && (need0 > caps.cap0 || need1 > caps.cap1 || needo > caps.max_out ||
-                             needb > caps.meta_bytes))
-        flush();
-      units.push_back(U);
-      tot_in += U.n_in;
-      for (int k = 0; k < D; ++k) tot[k] += U.n_pass[k];
-    }
   }
   flush();
   // the order in which the blocks of a launch take the chunks
@@ -409,8 +491,8 @@ double chunk_work(const unsigned char *blob_header, int dim, int p) {
   int64_t fib = 1;
   for (int d = 1; d < dim; ++d) fib *= p;
   double w = 1.0;
-  for (int k = 0; k < dim; ++k) {
-    const int64_t nf = hdr[k] * fib, nf2 = hdr[3 + k] * fib;
+  for (int j = 0; j < hdr[0] && j < kMaxPasses; ++j) {
+    const int64_t nf = hdr[4 + j] * fib, nf2 = hdr[4 + kMaxPasses + j] * fib;
     w += (double)((nf + 31) / 32 + (nf2 + 31) / 32) / kProgramWarps;
   }
   return w;
@@ -418,23 +500,28 @@ double chunk_work(const unsigned char *blob_header, int dim, int p) {
 
 std::string validate_program(const StageProgram &prog, int dim, int p, ChunkCaps caps, int64_t in_tiles,
                              int64_t out_tiles) {
+  (void)p;
   for (size_t ci = 0; ci < prog.chunks.size(); ++ci) {
     const ChunkDesc &c = prog.chunks[ci];
-    const int n0 = c.n_item[0], n1 = dim == 3 ? c.n_item[1] : 0, nl = c.n_item[dim - 1];
-    const int stage_cap = dim == 3 ? caps.cap1 : caps.cap0;  // outputs are staged there
-    if (c.n_in < 1 || c.n_in > caps.cap0 || n0 > caps.cap1 || n1 > caps.cap0 || nl > caps.max_out ||
-        nl > stage_cap)
-      return "chunk exceeds its shared-memory capacities";
     if (c.blob_off < 0 || (c.blob_off & 15) || (size_t)c.blob_off + kBlobHeader > prog.blob.size())
       return "metadata blob out of range";
     const int32_t *hdr = reinterpret_cast<const int32_t *>(prog.blob.data() + c.blob_off);
+    const int NP = hdr[0];
+    if (NP != c.n_pass || NP < dim || NP > kMaxPasses || NP % dim != 0) return "metadata header mismatch";
+    if (hdr[1] != c.n_in) return "metadata header mismatch";
+    int need0 = c.n_in, need1 = 0;
     int64_t nitems = 0;
-    for (int k = 0; k < dim; ++k) {
-      if (hdr[k] != c.n_item[k] || hdr[3 + k] < 0 || hdr[3 + k] > hdr[k]) return "metadata header mismatch";
-      nitems += hdr[k];
+    for (int j = 0; j < NP; ++j) {
+      const int ni = hdr[4 + j], n2 = hdr[4 + kMaxPasses + j];
+      if (ni < 0 || n2 < 0 || n2 > ni) return "metadata header mismatch";
+      if (j & 1) need0 = std::max(need0, ni);
+      else need1 = std::max(need1, ni);
+      nitems += ni;
     }
-    if (hdr[6] != c.n_in) return "metadata header mismatch";
-    const int n_oruns = hdr[7];
+    const int nl = hdr[4 + NP - 1];
+    if (c.n_in < 1 || need0 > caps.cap0 || need1 > caps.cap1 || nl > caps.max_out)
+      return "chunk exceeds its shared-memory capacities";
+    const int n_oruns = hdr[2];
     const int64_t need = (kBlobHeader + nitems * (int64_t)sizeof(Item) + n_oruns * (int64_t)sizeof(Run) + 15) & ~(int64_t)15;
     if (c.blob_bytes != need || c.blob_bytes > caps.meta_bytes || (size_t)c.blob_off + c.blob_bytes > prog.blob.size())
       return "metadata blob out of range";
@@ -459,22 +546,22 @@ std::string validate_program(const StageProgram &prog, int dim, int p, ChunkCaps
       covered += rn.count;
     }
     if (covered != nl) return "output runs do not cover the outputs";
-    int off = 0;
-    int nsrc = c.n_in;  // sources of pass k live in the previous pass's buffer
-    for (int k = 0; k < dim; ++k) {
-      const int ni = hdr[k], n2 = hdr[3 + k];
-      std::vector<char> seen(c.n_item[k], 0);
+    int64_t off = 0;
+    int nsrc = c.n_in;  // sources of pass j live in the previous pass's buffer
+    for (int j = 0; j < NP; ++j) {
+      const int ni = hdr[4 + j], n2 = hdr[4 + kMaxPasses + j];
+      std::vector<char> seen(ni, 0);
       for (int i = 0; i < ni; ++i) {
         const Item &it = items[off + i];
         if (it.src0 >= nsrc) return "item source 0 out of range";
         if ((i < n2) != (it.src1 != 0xffff)) return "two-source items do not lead the pass";
         if (it.src1 != 0xffff && it.src1 >= nsrc) return "item source 1 out of range";
         if (it.ops >= (it.src1 != 0xffff ? 16 : 4)) return "operator out of range";
-        if (it.dst >= c.n_item[k] || seen[it.dst]) return "item destination out of range or repeated";
+        if (it.dst >= ni || seen[it.dst]) return "item destination out of range or repeated";
         seen[it.dst] = 1;
       }
       off += ni;
-      nsrc = c.n_item[k];
+      nsrc = ni;
     }
   }
   return "";

@@ -7,13 +7,16 @@
 
 namespace bfly {
 
-// One block of work of the recursive step: a run of consecutive units (A', B), compiled
-// on the host into per-pass item lists (see make_stage_program).  Its metadata blob (a
-// 32-byte header {n_item[3], n_two[3], n_in, n_out_runs} (n_two: the leading
+// One block of work of the recursive step: a run of consecutive units, compiled on the
+// host into per-pass item lists (see make_step_program).  A step applies one level of the
+// recursion (D passes, one per axis) or two consecutive levels (2D passes; the tiles of the
+// level between them stay in shared memory).  Its metadata blob (a 64-byte header
+// {n_pass, n_in, n_out_runs, 0, n_item[kMaxPasses], n_two[kMaxPasses]} (n_two: the leading
 // two-source items of each pass), the items of every pass, then the output runs, padded
 // to 16 bytes) is copied to shared memory in one piece; its inputs are copied run by run,
 // its outputs written back run by run.
-constexpr int kBlobHeader = 32;
+constexpr int kBlobHeader = 64;
+constexpr int kMaxPasses = 6;
 // Consumer warps of a recursive-step block, which split every pass of a chunk.
 constexpr int kProgramWarps = 7;
 struct ChunkDesc {
@@ -22,7 +25,8 @@ struct ChunkDesc {
   int32_t run_off;    // first run in StageProgram::runs
   int32_t n_runs;
   int32_t n_in;       // input tiles (the runs' total)
-  int32_t n_item[3];  // items of pass 0 .. D-1 (the last pass writes the outputs)
+  int32_t n_pass;     // passes (the last writes the outputs)
+  int32_t pad[2];
 };
 static_assert(sizeof(ChunkDesc) == 32, "ChunkDesc is uploaded as 32 bytes");
 
@@ -65,9 +69,9 @@ struct StageProgram {
   std::vector<int32_t> in_off;      // per chunk: first entry of in_tiles
 };
 
-// Shared-memory capacities of one block, in tiles: an input buffer holds the inputs (and
-// the pass-1 results in 3D), the scratch buffer the pass-0 results; at most max_out
-// outputs; a metadata blob of at most meta_bytes.
+// Shared-memory capacities of one block, in tiles: pass j reads the buffer pass j-1 wrote
+// and writes the scratch buffer (even j) or the input buffer (odd j); the input buffer
+// first holds the inputs.  At most max_out outputs; a metadata blob of at most meta_bytes.
 struct ChunkCaps {
   int cap0, cap1, max_out, meta_bytes;
 };
@@ -111,19 +115,27 @@ void transfer_factors(int p, bool adjoint, double *W /* 2*p*p*2 */, double *phi 
 // G_{ll'} = e^{2 pi i l l'/q^2}, v(tau)_l = e^{2 pi i l tau/q}, tau in leaf widths.
 void leaf_weights(int p, double tau, double *w /* 2p doubles */);
 
-// The recursive step at stage t as chunk programs.  Forward: unit (A', B) reads the tiles
-// f^{A'Bc} of the children Bc of B and writes f^{AB} for the children A of A'; adjoint:
-// reads f^{AB} of the children A, writes f^{A'Bc}.  The operator of every (A, Bc) pair is
-// (x)_d C^{(gamma_d(A), delta_d(Bc))}; passes apply one axis each and sum, before each
-// axis, the sources that agree on all bits still to be applied (sum factorisation).
+// The trees of stage t of the recursive step:
 //   csAp : children of the A' boxes (T_X level L-t-1 -> L-t), xidx: box indices of level L-t
 //   csB  : children of the B boxes (T_K level t -> t+1),       kidx: box indices of level t+1
-//   in_row / out_row: tiles per row of the input / output stage buffer.
-// The chunks are runs of consecutive units, each as large as the capacities allow, listed
-// in the order of schedule_chunks.
-StageProgram make_stage_program(int dim, int p, const std::vector<int32_t> &csAp,
-                                const std::vector<int32_t> &xidx, const std::vector<int32_t> &csB,
-                                const std::vector<int32_t> &kidx, bool adjoint, ChunkCaps caps);
+struct StageTrees {
+  const std::vector<int32_t> *csAp, *xidx, *csB, *kidx;
+};
+
+// The recursive step as chunk programs, for one stage t (levels = 1, st[0] its trees) or
+// the two stages t and t-1 in one launch (levels = 2, st[0] and st[1]).  Forward, a unit
+// (A', B) of stage t reads the tiles f^{A'Bc} of the children Bc of B and writes f^{AB}
+// for the children A of A'; adjoint: reads f^{AB} of the children A, writes f^{A'Bc}.  The
+// operator of every (A, Bc) pair is (x)_d C^{(gamma_d(A), delta_d(Bc))}; passes apply one
+// axis each and sum, before each axis, the sources that agree on all bits still to be
+// applied (sum factorisation).  Two levels: unit (A'', B_) (A'' on the A' level of stage t,
+// B_ on the B level of stage t-1) groups the stage-t units (A'', B) for the children B of
+// B_ and the stage-(t-1) units (A, B_) for the children A of A'' (in the adjoint the
+// latter come first); the stage-t tiles between them are not written out.
+// The chunks are runs of consecutive units within the capacities, listed in the order of
+// schedule_chunks.  *fits (optional) becomes false when a single unit exceeds them.
+StageProgram make_step_program(int dim, int p, const StageTrees *st, int levels, bool adjoint, ChunkCaps caps,
+                               bool *fits = nullptr);
 
 // The order in which the persistent blocks of a launch take the chunks (indices into
 // work): decreasing work, so that the blocks that finish first take the smallest chunks

@@ -21,7 +21,12 @@ struct bfly_plan_s {
   bfly::ChunkCaps caps{};
   int level_grid = 0, TS = 0;
   size_t level_smem = 0, elem_bytes = 0;
-  std::vector<bfly::StageProgram> progF, progA;  // per stage t in [0, L-1]
+  // steps of the recursive step in forward order: stages t .. t - levels + 1 in one launch
+  struct Step {
+    int t, levels;
+  };
+  std::vector<Step> steps;
+  std::vector<bfly::StageProgram> progF, progA;  // per step
   std::vector<int64_t> pairs;              // per stage t in [0, L]
   // device memory: one allocation carved into the arrays below
   char *dmem = nullptr;
@@ -38,7 +43,9 @@ struct bfly_plan_s {
   int *status = nullptr;  // device status word (bfly_device_status)
   // work counters of the recursive-step launches, [direction][stage t][2] (LevelArgs::sched)
   unsigned long long *sched = nullptr;
-  std::vector<DevProg> dF, dA;  // per stage t in [0, L-1]
+  std::vector<DevProg> dF, dA;  // per step
+  // stage buffers: the charges between steps; boundary b (b = 0: stage L, b = s + 1: after
+  // forward step s, b = steps: stage 0) lives in buf[b mod 2]
   void *buf[2] = {nullptr, nullptr};
   void *stage_in = nullptr, *stage_out = nullptr;
   bfly_plan_info_t info{};
@@ -69,15 +76,18 @@ inline bfly::PointArgs point_args(bfly_plan_t P, bool x_side, const void *vin, v
   return a;
 }
 
-inline bfly::LevelArgs level_args(bfly_plan_t P, int t, bool adjoint, int nrhs) {
+// Arguments of step s (forward: from boundary s to s + 1; adjoint: the reverse).
+inline bfly::LevelArgs level_args(bfly_plan_t P, int s, bool adjoint, int nrhs) {
   bfly::LevelArgs a{};
-  void *bt = P->buf[t & 1], *bt1 = P->buf[(t + 1) & 1];
-  const bfly::StageProgram &pg = adjoint ? P->progA[t] : P->progF[t];
-  const bfly_plan_s::DevProg &dp = adjoint ? P->dA[t] : P->dF[t];
-  a.in = adjoint ? bt : bt1;
-  a.out = adjoint ? bt1 : bt;
-  a.in_rhs = (adjoint ? P->pairs[t] : P->pairs[t + 1]) * P->TS;
-  a.out_rhs = (adjoint ? P->pairs[t + 1] : P->pairs[t]) * P->TS;
+  const bfly_plan_s::Step &st = P->steps[s];
+  const int t_hi = st.t + 1, t_lo = st.t - st.levels + 1;  // stages of the boundaries
+  void *b0 = P->buf[s & 1], *b1 = P->buf[(s + 1) & 1];
+  const bfly::StageProgram &pg = adjoint ? P->progA[s] : P->progF[s];
+  const bfly_plan_s::DevProg &dp = adjoint ? P->dA[s] : P->dF[s];
+  a.in = adjoint ? b1 : b0;
+  a.out = adjoint ? b0 : b1;
+  a.in_rhs = (adjoint ? P->pairs[t_lo] : P->pairs[t_hi]) * P->TS;
+  a.out_rhs = (adjoint ? P->pairs[t_hi] : P->pairs[t_lo]) * P->TS;
   a.nrhs = nrhs;
   a.chunks = dp.chunks;
   a.nchunks = (int)pg.chunks.size();
@@ -91,7 +101,7 @@ inline bfly::LevelArgs level_args(bfly_plan_t P, int t, bool adjoint, int nrhs) 
   a.wait_limit = stall ? 2000000LL : 2000000000LL;  // ~1 ms / ~1 s of SM clock
   a.status = P->status;
   a.inject_stall = stall ? 1 : 0;
-  a.sched = P->sched + ((adjoint ? (size_t)P->L : 0) + (size_t)t) * 2;
+  a.sched = P->sched + ((adjoint ? P->steps.size() : 0) + (size_t)s) * 2;
   return a;
 }
 

@@ -37,7 +37,7 @@ class PlanInfo(ctypes.Structure):
                 ("flops_fwd", ctypes.c_double), ("lane_use_fwd", ctypes.c_double),
                 ("smem_kb", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("tuned_ms", ctypes.c_double),
-                ("plan_seconds", ctypes.c_double)]
+                ("plan_seconds", ctypes.c_double), ("steps", ctypes.c_int)]
 
 
 SIGNATURES = {

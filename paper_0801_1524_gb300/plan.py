@@ -157,8 +157,8 @@ class Plan:
         return self._run(fn, v, n_in, n_out, out, stream, "bfly_direct")
 
     def with_events(self, v, events, adjoint: bool = False, out=None, stream=None):
-        """bfly_execute_events: records the torch.cuda.Event list `events` (L + 3 of them,
-        already recorded once so that they exist) around every kernel launch."""
+        """bfly_execute_events: records the torch.cuda.Event list `events` (info()["steps"]
+        + 3 of them, already recorded once so that they exist) around every kernel launch."""
         arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
         fn = lambda h, a, b, n, dt, st: self._lib.bfly_execute_events(h, a, b, n, dt, int(adjoint),
                                                                       st, arr, len(events))

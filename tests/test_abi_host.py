@@ -99,6 +99,20 @@ def test_curve_workload_plan_counts():
     assert all(a * b <= 12 * inst.N for _, a, b in st)
     assert info["tiles_written_fwd"] == sum(a * b for t, a, b in st if t < 13)
     assert info["plan_seconds"] < 5.0
+    # stage 12 alone, then the pairs (11, 10) .. (1, 0): 7 launches of the recursive step
+    assert info["steps"] == 7
+
+
+@pytest.mark.parametrize("dim,N,p,expect", [(2, 1.0, 5, 0), (2, 2.0, 5, 1), (2, 4.0, 7, 1), (2, 8.0, 7, 2),
+                                            (2, 1000.5, 7, 5), (3, 16.0, 5, 4), (3, 12.0, 3, 4)])
+def test_recursive_step_launch_count(dim, N, p, expect):
+    # 2D: two stages per launch ((1, 0), (3, 2), ..., the top stage alone when L is odd);
+    # 3D: one stage per launch.  Every program passed validation at plan creation.
+    inst = w.small_random(dim, N, p, 200, 150, 9, edge_fraction=0.3)
+    P = Plan(inst.x, inst.k, N, p, host_only=True)
+    info = P.info()
+    assert info["steps"] == expect
+    assert info["steps"] == ((info["L"] + 1) // 2 if dim == 2 else info["L"])
 
 
 @pytest.mark.parametrize("nx,nk", [(0, 40), (40, 0), (0, 0)])

@@ -176,6 +176,30 @@ def test_execute_host_matches_device():
     assert np.array_equal(ua, P.adjoint(_gpu(host, torch.complex64)).cpu().numpy())
 
 
+@pytest.mark.parametrize("dim,N,p", [(2, 4096.0, 7), (2, 2048.0, 5), (3, 64.0, 5)])
+def test_events_path_matches_and_counts_launches(dim, N, p):
+    # bfly_execute_events: one event before every launch (leaf, the recursive-step launches
+    # of one or two stages each, final) and one after; same results as bfly_execute
+    inst = w.small_random(dim, N, p, 600, 500, 21)
+    f = _gpu(inst.sources()[0], torch.complex64)
+    P = _plan(inst, "fp32")
+    info = P.info()
+    L, S = info["L"], info["steps"]
+    assert S == ((L + 1) // 2 if dim == 2 else L)
+    for adjoint in (False, True):
+        v = f if not adjoint else P.forward(f)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(S + 3)]
+        for e in ev:
+            e.record()
+        got = P.with_events(v, ev, adjoint=adjoint)
+        torch.cuda.synchronize()
+        ref = P.adjoint(v) if adjoint else P.forward(v)
+        assert torch.equal(got, ref)
+        assert all(ev[i].elapsed_time(ev[i + 1]) >= 0.0 for i in range(S + 2))
+    with pytest.raises(RuntimeError):
+        P.with_events(f, [torch.cuda.Event(enable_timing=True) for _ in range(L + 3 + (S == L))])
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_empty_sides(prec):
     # no sources: every potential is zero; no targets: an empty result; the adjoint mirrors
