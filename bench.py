@@ -1,8 +1,8 @@
 #!/usr/bin/env python3
 """Benchmark of the butterfly sparse Fourier transform on one GB300.
 
-Workload (one "step" = one whole transform: leaf step, the L recursive stages in one- or
-two-stage launches, final step): 2D, N = 8192, X = circle of radius 0.4 (82,355 targets), K = ellipse 0.45 x 0.3
+Workload (one "step" = one whole transform: leaf step, the L recursive stages in launches
+of up to three stages, final step): 2D, N = 8192, X = circle of radius 0.4 (82,355 targets), K = ellipse 0.45 x 0.3
 with a 0.03 sin(5 theta) radial perturbation (80,962 sources), p = 7, one right-hand side
 of complex64 Gaussian sources, FP32 arithmetic with FP64-built operators.
 
@@ -184,23 +184,6 @@ def replica_value(world, ms):
 
 
 # ---------------------------------------------------------------------------- main arm
-def step_stages(L, dim, S):
-    """(t, levels) of the recursive-step launches when the plan follows the default split
-    (2D: stage L-1 alone when L is odd, then pairs down to (1, 0); 3D: one stage each),
-    else None."""
-    if dim == 3:
-        out = [(t, 1) for t in range(L - 1, -1, -1)]
-    else:
-        out, t = [], L - 1
-        if L % 2 == 1:
-            out.append((t, 1))
-            t -= 1
-        while t >= 1:
-            out.append((t, 2))
-            t -= 2
-    return out if len(out) == S else None
-
-
 def main_bfly(args, rank, world, dist):
     import torch
     from paper_0801_1524_gb300.plan import Plan
@@ -362,12 +345,9 @@ def main_bfly(args, rank, world, dist):
     # inside a two-stage launch stays in shared memory)
     flops = info["jobs_fwd"] * (2 * p ** 3 if d == 2 else 3 * p ** 4) * 8.0
     flops_exec = info["flops_fwd"]     # as executed (sum factorisation shares work)
-    steps = step_stages(L, d, S)
+    steps = plan.steps()
     pairs = {t: a * b for t, a, b in plan.stages()}
-    if steps is not None:
-        bytes_ = sum(pairs[t + 1] + pairs[t - lev + 1] for t, lev in steps) * PD * 8.0
-    else:
-        bytes_ = (info["tiles_read_fwd"] + info["tiles_written_fwd"]) * PD * 8.0
+    bytes_ = sum(pairs[t + 1] + pairs[t - lev + 1] for t, lev in steps) * PD * 8.0
     level_s = float(np.mean(level_ms)) * 1e-3
     per_launch_s = level_s / S
     hbm_peak, hbm_src = peaks()
@@ -384,16 +364,16 @@ def main_bfly(args, rank, world, dist):
     main, alt = (roof_alu, roof_hbm) if roof_alu["frac"] >= roof_hbm["frac"] else (roof_hbm, roof_alu)
     main["traffic"] = traffic
     alt["traffic"] = traffic
-    main["kernel"] = (f"level_kernel<float,{d},{p}> (recursive step, {S} launches: "
-                      + ("one or two stages each)" if d == 2 else "one stage each)"))
+    main["kernel"] = (f"level_kernel<float,{d},{p}> (recursive step, {S} launches of "
+                      + "/".join(str(lev) for _, lev in steps) + " stages)")
     main["algorithmic_per_launch"] = {"flops": flops / S, "bytes": bytes_ / S,
                                       "executed_flops": flops_exec / S}
     main["duration"] = ("mean per-launch CUDA-event time of the recursive step, from a second pass "
                         "of the same steps with an event between consecutive launches")
     alt["kernel"] = main["kernel"]
     out["roofline_alt"] = alt
-    kern_names = (["leaf"] + ([f"level_t{t}" + (f"-{t - 1}" if lev == 2 else "") for t, lev in steps]
-                              if steps is not None else [f"level_{i}" for i in range(S)]) + ["final"])
+    kern_names = (["leaf"] + [f"level_t{t}" + (f"-{t - lev + 1}" if lev > 1 else "") for t, lev in steps]
+                  + ["final"])
     out["kernel_ms"] = {n: float(v) for n, v in zip(kern_names, kern_ms.mean(axis=0))}
 
     value = replica_value(world, ms)

@@ -91,8 +91,8 @@ typedef struct {
   int blocks_per_sm;            /* resident blocks of the recursive step per SM */
   double tuned_ms;              /* autotuning: time of the chosen candidate (0 if not tuned) */
   double plan_seconds;          /* host wall time of bfly_plan_create */
-  int steps;                    /* launches of the recursive step per transform: one or two
-                                   stages each (two where their units fit the capacities) */
+  int steps;                    /* launches of the recursive step per transform: up to three
+                                   stages each in 2D, one in 3D (bfly_plan_step) */
 } bfly_plan_info_t;
 
 /*
@@ -238,6 +238,14 @@ void bfly_batch_destroy(bfly_batch_t batch);
 
 /* Sizes and counts of the plan (host data; no device access). */
 bfly_status bfly_plan_info(bfly_plan_t plan, bfly_plan_info_t *info);
+
+/*
+ * bfly_plan_step — the stages of launch s (0 <= s < steps) of the recursive step in the
+ * forward sweep: stages *t, *t - 1, .., *t - *levels + 1 (Sec. 2.2 step 3, one launch for
+ * them; the adjoint sweep runs the launches in reverse).  BFLY_ERR_INVALID_ARG for s out
+ * of range or a NULL pointer.
+ */
+bfly_status bfly_plan_step(bfly_plan_t plan, int s, int *t, int *levels);
 
 /* Stage t (0..L): number of non-empty T_X boxes at level L-t (nA) and T_K boxes at
  * level t (nB); the stage holds nA*nB equivalent-charge tiles. */

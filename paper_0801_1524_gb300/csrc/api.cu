@@ -1,6 +1,7 @@
 // C ABI of the butterfly (include/bfly.h): plan creation, upload and the execution entry
 // points.  Every step of the transform runs in the kernels of this library.
 #include <algorithm>
+#include <deque>
 #include <chrono>
 #include <cstdlib>
 #include <cmath>
@@ -245,42 +246,39 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     P->level_grid = blocks * sms;
     I.blocks_per_sm = blocks;
   }
-  // steps of the sweep (forward order).  2D: two stages per launch, (1, 0), (3, 2), ...
-  // from the bottom, and stage L-1 alone when L is odd; a pair whose units exceed the
-  // shared-memory capacities runs as two one-stage steps.  3D: one stage per launch (a
-  // two-level unit holds up to 64 input tiles, more than a block's share of shared memory)
+  // steps of the sweep (forward order).  2D: three stages per launch, (2, 1, 0), (5, 4, 3),
+  // ... from the bottom and the L mod 3 top stages together; a step whose units exceed the
+  // shared-memory capacities gives up its last stage to a step of its own.  3D: one stage
+  // per launch (a two-level unit holds up to 64 input tiles, more than a block's share of
+  // shared memory)
   auto trees = [&](int t) {
     return bfly::StageTrees{&P->TX.cs[L - t - 1], &P->TX.idx[L - t], &P->TK.cs[t], &P->TK.idx[t + 1]};
   };
-  std::vector<bfly_plan_s::Step> plan_steps;
-  {
-    int t = L - 1;
-    if (dim == 3)
-      for (; t >= 0; --t) plan_steps.push_back({t, 1});
-    if (L % 2 == 1 && t >= 0) plan_steps.push_back({t--, 1});
-    for (; t >= 1; t -= 2) plan_steps.push_back({t, 2});
+  std::deque<int> todo;
+  if (dim == 3) {
+    todo.assign(L, 1);
+  } else {
+    if (L % bfly::kMaxLevels) todo.push_back(L % bfly::kMaxLevels);
+    for (int i = 0; i < L / bfly::kMaxLevels; ++i) todo.push_back(bfly::kMaxLevels);
   }
+  std::vector<bfly_plan_s::Step> plan_steps;
   int64_t lanes_used_all = 0, lanes_issued_all = 0;
-  for (size_t si = 0; si < plan_steps.size(); ++si) {
-    const int t = plan_steps[si].t;
+  for (int t = L - 1; !todo.empty();) {
+    int lev = todo.front();
+    todo.pop_front();
     bfly::StageProgram pf, pa;
-    bool ok = false;
-    if (plan_steps[si].levels == 2) {
-      const bfly::StageTrees st2[2] = {trees(t), trees(t - 1)};
+    for (;;) {
+      bfly::StageTrees st[bfly::kMaxLevels];
+      for (int l = 0; l < lev; ++l) st[l] = trees(t - l);
       bool fits_f = true, fits_a = true;
-      pf = bfly::make_step_program(dim, p, st2, 2, false, caps, &fits_f);
-      pa = bfly::make_step_program(dim, p, st2, 2, true, caps, &fits_a);
-      ok = fits_f && fits_a;
-      if (!ok) {
-        plan_steps[si].levels = 1;
-        plan_steps.insert(plan_steps.begin() + si + 1, bfly_plan_s::Step{t - 1, 1});
-      }
+      pf = bfly::make_step_program(dim, p, st, lev, false, caps, &fits_f);
+      pa = bfly::make_step_program(dim, p, st, lev, true, caps, &fits_a);
+      if ((fits_f && fits_a) || lev == 1) break;
+      --lev;
+      todo.push_front(1);
     }
-    if (!ok) {
-      const bfly::StageTrees st1 = trees(t);
-      pf = bfly::make_step_program(dim, p, &st1, 1, false, caps);
-      pa = bfly::make_step_program(dim, p, &st1, 1, true, caps);
-    }
+    plan_steps.push_back({t, lev});
+    const size_t si = plan_steps.size() - 1;
     const int t_lo = t - plan_steps[si].levels + 1;
     for (int dir = 0; dir < 2; ++dir) {
       const int64_t tin = dir ? P->pairs[t_lo] : P->pairs[t + 1], tout = dir ? P->pairs[t + 1] : P->pairs[t_lo];
@@ -313,6 +311,7 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     I.flops_fwd += (double)srcs * fib * (8.0 * p * (p - 1) / 2 + 2.0 * (p + 1) / 2);
     P->progF.push_back(std::move(pf));
     P->progA.push_back(std::move(pa));
+    t -= lev;
   }
   P->steps = plan_steps;
   I.steps = (int)plan_steps.size();
@@ -568,6 +567,14 @@ bfly_status bfly_device_status(bfly_plan_t plan, int *flags) {
 bfly_status bfly_plan_info(bfly_plan_t plan, bfly_plan_info_t *info) {
   if (!plan || !info) return fail(BFLY_ERR_INVALID_ARG, "plan or info is NULL");
   *info = plan->info;
+  return BFLY_OK;
+}
+
+bfly_status bfly_plan_step(bfly_plan_t plan, int s, int *t, int *levels) {
+  if (!plan || !t || !levels) return fail(BFLY_ERR_INVALID_ARG, "NULL argument");
+  if (s < 0 || s >= (int)plan->steps.size()) return fail(BFLY_ERR_INVALID_ARG, "step outside 0..steps-1");
+  *t = plan->steps[s].t;
+  *levels = plan->steps[s].levels;
   return BFLY_OK;
 }
 

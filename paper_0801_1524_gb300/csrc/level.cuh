@@ -64,9 +64,9 @@ struct LevelShape {
   static constexpr size_t tile_bytes = (size_t)TS * sizeof(C);
   static int meta_bytes(int cap0, int cap1, int max_out) {
     // header, an item (8 bytes) per pass tile, one run (8 bytes) per output, padding.  In
-    // 2D a step has up to two levels (passes into scratch, input, scratch buffers and the
-    // staged outputs); in 3D one (scratch, input, staged outputs)
-    const int items = (D == 2 ? 2 * cap1 + cap0 : cap1 + cap0) + max_out;
+    // 2D a step has up to three levels (passes alternately into the scratch and input
+    // buffers, the last into the staged outputs); in 3D one
+    const int items = (D == 2 ? 3 * cap1 + 2 * cap0 : cap1 + cap0) + max_out;
     return (kBlobHeader + 8 * items + 8 * max_out + 15) & ~15;
   }
   // 4 mbarriers | 2 metadata slots | 2 input buffers | scratch (2 in 3D, where a

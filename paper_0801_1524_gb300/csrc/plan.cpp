@@ -246,7 +246,7 @@ UnitProg build_unit(int D, const StageTrees &S, int64_t iAp, int64_t iB, bool ad
 
 // A unit of a step: its subunits level by level (one level: a single unit).
 struct StepUnit {
-  std::vector<UnitProg> lev[2];
+  std::vector<UnitProg> lev[kMaxLevels];
 };
 
 }  // namespace
@@ -285,7 +285,7 @@ StageProgram make_step_program(int dim, int p, const StageTrees *st, int levels,
   auto flush = [&]() {
     if (cur.empty()) return;
     ChunkDesc cd{};
-    std::vector<const UnitProg *> su[2];
+    std::vector<const UnitProg *> su[kMaxLevels];
     for (const StepUnit &m : cur)
       for (int l = 0; l < NL; ++l)
         for (const UnitProg &u : m.lev[l]) su[l].push_back(&u);
@@ -314,7 +314,7 @@ StageProgram make_step_program(int dim, int p, const StageTrees *st, int levels,
     }
     cd.n_runs = (int32_t)prog.runs.size() - cd.run_off;
     // output slots of every pass, numbered subunit by subunit
-    std::vector<int> base[2][3];
+    std::vector<int> base[kMaxLevels][3];
     for (int l = 0; l < NL; ++l)
       for (int k = 0; k < D; ++k) {
         base[l][k].resize(su[l].size());
@@ -434,33 +434,37 @@ StageProgram make_step_program(int dim, int p, const StageTrees *st, int levels,
     tot = t2;
   };
 
-  if (NL == 1) {
-    const StageTrees &S = st[0];
-    const int64_t nAp = (int64_t)S.csAp->size() - 1, nB = (int64_t)S.csB->size() - 1;
-    for (int64_t iAp = 0; iAp < nAp; ++iAp)
-      for (int64_t iB = 0; iB < nB; ++iB) {
-        StepUnit m;
-        m.lev[0].push_back(build_unit(D, S, iAp, iB, adjoint));
-        push(std::move(m));
+  // stages t, t-1, .. (trees st[0], st[1], ..): unit (A_top, B_bot) with A_top a box of
+  // the A' level of stage t and B_bot one of the B level of stage t-NL+1.  Its level l
+  // (stage t-l) units are (A, B) for the descendants A of A_top l levels down and B of
+  // B_bot NL-1-l levels down; the tiles of the stages between levels stay in shared
+  // memory.  The adjoint runs the levels in the reverse order.
+  const int64_t n_top = (int64_t)st[0].csAp->size() - 1, n_bot = (int64_t)st[NL - 1].csB->size() - 1;
+  std::vector<int32_t> As[kMaxLevels], Bs[kMaxLevels];
+  for (int64_t iA = 0; iA < n_top; ++iA) {
+    As[0].assign(1, (int32_t)iA);
+    for (int l = 1; l < NL; ++l) {  // children along the A' levels of stages t, t-1, ..
+      const std::vector<int32_t> &cs = *st[l - 1].csAp;
+      As[l].clear();
+      for (int32_t a : As[l - 1])
+        for (int32_t c = cs[a]; c < cs[a + 1]; ++c) As[l].push_back(c);
+    }
+    for (int64_t iB = 0; iB < n_bot; ++iB) {
+      Bs[NL - 1].assign(1, (int32_t)iB);
+      for (int l = NL - 2; l >= 0; --l) {  // children along the B levels of stages t-NL+1, ..
+        const std::vector<int32_t> &cs = *st[l + 1].csB;
+        Bs[l].clear();
+        for (int32_t b : Bs[l + 1])
+          for (int32_t c = cs[b]; c < cs[b + 1]; ++c) Bs[l].push_back(c);
       }
-  } else {
-    // stages t (trees st[0]) and t-1 (st[1]): unit (A'', B_) with A'' a box of the A'
-    // level of stage t and B_ one of the B level of stage t-1.  Its stage-t units are
-    // (A'', B) for the children B of B_, its stage-(t-1) units (A, B_) for the children
-    // A of A''; the stage-t tiles f^{A B} between them stay in shared memory.
-    const StageTrees &Shi = st[0], &Slo = st[1];
-    const int64_t nA2 = (int64_t)Shi.csAp->size() - 1, nB2 = (int64_t)Slo.csB->size() - 1;
-    for (int64_t iA2 = 0; iA2 < nA2; ++iA2)
-      for (int64_t iB2 = 0; iB2 < nB2; ++iB2) {
-        StepUnit m;
-        std::vector<UnitProg> hiU, loU;
-        for (int32_t b = (*Slo.csB)[iB2]; b < (*Slo.csB)[iB2 + 1]; ++b) hiU.push_back(build_unit(D, Shi, iA2, b, adjoint));
-        for (int32_t a = (*Shi.csAp)[iA2]; a < (*Shi.csAp)[iA2 + 1]; ++a) loU.push_back(build_unit(D, Slo, a, iB2, adjoint));
-        // forward: stage t first; adjoint: the adjoint of stage t-1 first
-        m.lev[0] = adjoint ? std::move(loU) : std::move(hiU);
-        m.lev[1] = adjoint ? std::move(hiU) : std::move(loU);
-        push(std::move(m));
+      StepUnit m;
+      for (int l = 0; l < NL; ++l) {
+        std::vector<UnitProg> &dst = m.lev[adjoint ? NL - 1 - l : l];
+        for (int32_t a : As[l])
+          for (int32_t b : Bs[l]) dst.push_back(build_unit(D, st[l], a, b, adjoint));
       }
+      push(std::move(m));
+    }
   }
   flush();
   // the order in which the blocks of a launch take the chunks

@@ -17,6 +17,7 @@ namespace bfly {
 // its outputs written back run by run.
 constexpr int kBlobHeader = 64;
 constexpr int kMaxPasses = 6;
+constexpr int kMaxLevels = 3;  // stages per launch (2D; 3D: one)
 // Consumer warps of a recursive-step block, which split every pass of a chunk.
 constexpr int kProgramWarps = 7;
 struct ChunkDesc {
@@ -122,16 +123,17 @@ struct StageTrees {
   const std::vector<int32_t> *csAp, *xidx, *csB, *kidx;
 };
 
-// The recursive step as chunk programs, for one stage t (levels = 1, st[0] its trees) or
-// the two stages t and t-1 in one launch (levels = 2, st[0] and st[1]).  Forward, a unit
-// (A', B) of stage t reads the tiles f^{A'Bc} of the children Bc of B and writes f^{AB}
-// for the children A of A'; adjoint: reads f^{AB} of the children A, writes f^{A'Bc}.  The
-// operator of every (A, Bc) pair is (x)_d C^{(gamma_d(A), delta_d(Bc))}; passes apply one
-// axis each and sum, before each axis, the sources that agree on all bits still to be
-// applied (sum factorisation).  Two levels: unit (A'', B_) (A'' on the A' level of stage t,
-// B_ on the B level of stage t-1) groups the stage-t units (A'', B) for the children B of
-// B_ and the stage-(t-1) units (A, B_) for the children A of A'' (in the adjoint the
-// latter come first); the stage-t tiles between them are not written out.
+// The recursive step as chunk programs, for the `levels` consecutive stages t, t-1, ..
+// (st[l]: the trees of stage t-l; levels * dim <= kMaxPasses) in one launch.  Forward, a
+// unit (A', B) of stage t reads the tiles f^{A'Bc} of the children Bc of B and writes
+// f^{AB} for the children A of A'; adjoint: reads f^{AB} of the children A, writes
+// f^{A'Bc}.  The operator of every (A, Bc) pair is (x)_d C^{(gamma_d(A), delta_d(Bc))};
+// passes apply one axis each and sum, before each axis, the sources that agree on all
+// bits still to be applied (sum factorisation).  Several levels: unit (A_top, B_bot)
+// (A_top on the A' level of stage t, B_bot on the B level of the last stage) groups, for
+// every level l, the stage-(t-l) units (A, B) with A a descendant of A_top l levels down
+// and B one of B_bot levels-1-l levels down (the adjoint runs the levels in reverse);
+// the tiles of the stages between levels are not written out.
 // The chunks are runs of consecutive units within the capacities, listed in the order of
 // schedule_chunks.  *fits (optional) becomes false when a single unit exceeds them.
 StageProgram make_step_program(int dim, int p, const StageTrees *st, int levels, bool adjoint, ChunkCaps caps,

@@ -57,6 +57,7 @@ SIGNATURES = {
     "bfly_batch_destroy": (None, [_vp]),
     "bfly_device_status": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "bfly_plan_stage": (_i, [_vp, _i, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "bfly_plan_step": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "bfly_last_error": (ctypes.c_char_p, []),
     "bfly_version": (ctypes.c_char_p, []),
 }

@@ -104,6 +104,16 @@ class Plan:
         native.check(self._lib.bfly_plan_info(self._h, ctypes.byref(inf)), "bfly_plan_info")
         return {name: getattr(inf, name) for name, _ in native.PlanInfo._fields_}
 
+    def steps(self) -> list:
+        """[(t, levels)] per launch of the recursive step (forward order): stages t .. t-levels+1."""
+        out = []
+        for s in range(self.info()["steps"]):
+            t, lev = ctypes.c_int(), ctypes.c_int()
+            native.check(self._lib.bfly_plan_step(self._h, s, ctypes.byref(t), ctypes.byref(lev)),
+                         "bfly_plan_step")
+            out.append((t.value, lev.value))
+        return out
+
     def stages(self) -> list:
         """[(t, nA, nB)] for t = 0..L: stage t pairs nA T_X boxes with nB T_K boxes."""
         out = []

