@@ -505,6 +505,9 @@ double chunk_work(const unsigned char *blob_header, int dim, int p) {
 std::string validate_program(const StageProgram &prog, int dim, int p, ChunkCaps caps, int64_t in_tiles,
                              int64_t out_tiles) {
   (void)p;
+  // every tile of the input stage is read by exactly one chunk and every tile of the
+  // output stage written by exactly one (each pair of a stage belongs to one unit)
+  std::vector<unsigned char> read((size_t)std::max<int64_t>(in_tiles, 0), 0), written((size_t)std::max<int64_t>(out_tiles, 0), 0);
   for (size_t ci = 0; ci < prog.chunks.size(); ++ci) {
     const ChunkDesc &c = prog.chunks[ci];
     if (c.blob_off < 0 || (c.blob_off & 15) || (size_t)c.blob_off + kBlobHeader > prog.blob.size())
@@ -536,6 +539,8 @@ std::string validate_program(const StageProgram &prog, int dim, int p, ChunkCaps
       const Run &rn = prog.runs[c.run_off + r];
       if (rn.slot != covered || rn.count < 1 || rn.start < 0 || rn.start + (int64_t)rn.count > in_tiles)
         return "input run out of range";
+      for (int q = 0; q < rn.count; ++q)
+        if (read[rn.start + q]++) return "an input tile is read by two chunks";
       covered += rn.count;
     }
     if (covered != c.n_in) return "runs do not cover the inputs";
@@ -547,6 +552,8 @@ std::string validate_program(const StageProgram &prog, int dim, int p, ChunkCaps
       const Run &rn = oruns[r];
       if (rn.slot != covered || rn.count < 1 || rn.start < 0 || rn.start + (int64_t)rn.count > out_tiles)
         return "output run out of range";
+      for (int q = 0; q < rn.count; ++q)
+        if (written[rn.start + q]++) return "an output tile is written by two chunks";
       covered += rn.count;
     }
     if (covered != nl) return "output runs do not cover the outputs";
@@ -568,6 +575,10 @@ std::string validate_program(const StageProgram &prog, int dim, int p, ChunkCaps
       nsrc = ni;
     }
   }
+  for (unsigned char v : read)
+    if (!v) return "an input tile is read by no chunk";
+  for (unsigned char v : written)
+    if (!v) return "an output tile is written by no chunk";
   return "";
 }
 

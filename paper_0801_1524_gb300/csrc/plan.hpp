@@ -149,8 +149,9 @@ std::vector<size_t> schedule_chunks(const std::vector<double> &work);
 // the kProgramWarps consumer warps that share them.
 double chunk_work(const unsigned char *blob_header, int dim, int p);
 
-// Checks every index of a compiled stage program against the capacities it was compiled
-// for and the number of tiles of its input and output stage buffers; returns "" or a
+// Checks every index of a compiled step program against the capacities it was compiled
+// for and the number of tiles of its input and output stage buffers, and that every input
+// tile is read and every output tile written by exactly one chunk; returns "" or a
 // description of the first violation.
 std::string validate_program(const StageProgram &prog, int dim, int p, ChunkCaps caps, int64_t in_tiles,
                              int64_t out_tiles);
