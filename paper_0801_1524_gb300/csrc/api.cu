@@ -330,23 +330,6 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
       if (n2 != m) den *= std::sin(M_PI * ((double)(m - n2) / ((double)q * q)));
     inv_den[m] = 1.0 / den;
   }
-  std::vector<double> tabF = bfly::transfer_table(p, false), tabH = bfly::transfer_table(p, true);
-  // FP32 operators for the recursive step: [op][l][m], m padded to an even count
-  std::vector<float> tabF32, tabH32;
-  if (o.prec == BFLY_PREC_FP32) {
-    const int pp = (p + 1) & ~1, nops = 4;
-    tabF32.assign((size_t)nops * p * pp * 2, 0.0f);
-    tabH32.assign(tabF32.size(), 0.0f);
-    for (int op = 0; op < nops; ++op)
-      for (int m = 0; m < p; ++m)
-        for (int l = 0; l < p; ++l)
-          for (int c = 0; c < 2; ++c) {
-            const size_t from = (((size_t)op * p + m) * p + l) * 2 + c;
-            const size_t to = (((size_t)op * p + l) * pp + m) * 2 + c;
-            tabF32[to] = (float)tabF[from];
-            tabH32[to] = (float)tabH[from];
-          }
-  }
   std::vector<double> xs(x, x + nx * dim), kv(k, k + nk * dim);
 
   Arena A;
@@ -361,13 +344,6 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   A.add_vec(&P->xs, xs);
   A.add_vec(&P->ks_, kv);
   A.add_vec(&P->inv_den, inv_den);
-  if (o.prec == BFLY_PREC_FP32) {
-    A.add(&P->table, tabF32.size() * sizeof(float), tabF32.data());
-    A.add(&P->tableH, tabH32.size() * sizeof(float), tabH32.data());
-  } else {
-    A.add(&P->table, tabF.size() * sizeof(double), tabF.data());
-    A.add(&P->tableH, tabH.size() * sizeof(double), tabH.data());
-  }
   A.add(&P->Wx, (size_t)nx * dim * p * P->elem_bytes);
   A.add(&P->Wk, (size_t)nk * dim * p * P->elem_bytes);
   const size_t n_steps = P->steps.size();

@@ -66,7 +66,6 @@ bfly_status launch_all(bfly_batch_t B, const void *const *f, void *const *u, int
     a.nrhs = nrhs;
     a.entries = B->entries[t];
     a.nchunks = B->n_entries[t];
-    a.table = P0->table;
     a.cap0 = P0->caps.cap0;
     a.cap1 = P0->caps.cap1;
     a.meta_bytes = B->meta_bytes;

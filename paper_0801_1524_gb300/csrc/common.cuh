@@ -130,7 +130,6 @@ struct LevelArgs {
   int nchunks;
   const unsigned char *blob;    // per-chunk metadata blobs (plan.hpp)
   const Run *runs;
-  const void *table;            // [4][P][P] complex operators (conjugate-transposed: adjoint)
   int cap0, cap1, meta_bytes;   // shared-memory capacities the program was compiled for
   long long wait_limit;         // clock cycles before a wait gives up
   int *status;                  // device status word: bits set on a timeout

@@ -16,7 +16,7 @@ struct KernelSet {
   cudaError_t (*level_setup)(size_t smem, int *blocks_per_sm);
   size_t (*level_smem)(const ChunkCaps &caps);
   int (*meta_bytes)(int cap0, int cap1, int max_out);
-  size_t level_table_bytes, level_tile_bytes;
+  size_t level_tile_bytes;
   int tile_stride;  // complex elements per stored charge tile
   cudaError_t (*spread)(const PointArgs &a, cudaStream_t s);
   cudaError_t (*interp)(const PointArgs &a, cudaStream_t s);

@@ -109,8 +109,7 @@ struct Impl {
     return launch_dependent(interp_kernel<R, D, P>, grid, dim3(kPointThreads), 0, s, a);
   }
   static const KernelSet *get() {
-    static const KernelSet ks = {&level,         &level_setup,  &level_smem, &meta_bytes,
-                                 S::table_bytes, S::tile_bytes, S::TS,      &spread,
+    static const KernelSet ks = {&level, &level_setup, &level_smem, &meta_bytes, S::tile_bytes, S::TS, &spread,
                                  &interp};
     return &ks;
   }

@@ -60,7 +60,6 @@ struct LevelShape {
   static constexpr int PD = ipow(P, D);
   static constexpr int TS = tile_stride<R>(PD);
   static constexpr int FIB = PD / P;  // fibres of one tile along one axis
-  static constexpr size_t table_bytes = (size_t)NOPS * P * P * sizeof(C);  // as C^{(gamma,delta)}
   static constexpr size_t tile_bytes = (size_t)TS * sizeof(C);
   static int meta_bytes(int cap0, int cap1, int max_out) {
     // header, an item (8 bytes) per pass tile, one run (8 bytes) per output, padding.  In

@@ -122,40 +122,6 @@ void transfer_factors(int p, bool adjoint, double *W, double *phi) {
     }
 }
 
-std::vector<double> transfer_table(int p, bool adjoint) {
-  // Per axis, for A (index a, width w^A) and B (width w^B) with w^A w^B = N, the matching
-  // condition of Sec. 2.1 with the evaluation of Fig. 1 gives f^{AB} = T f^{A'Bc},
-  //   T_{ml} = e^{-2 pi i a m/q} w_m(tau_l) e^{2 pi i a tau_l},  tau_l = (delta + l/q)/2
-  // (the index of B cancels; eqs. M1 and E1).  With the rescaled charges
-  // g^{AB}_m = e^{2 pi i a m/q} f^{AB}_m and a = 2a' + gamma this becomes
-  //   g^{AB} = C(gamma, delta) g^{A'Bc},  C(gamma, delta)_{ml} = w_m(tau_l) e^{2 pi i gamma tau_l}
-  // (the remaining factor e^{2 pi i a' delta} is 1): four operators per axis whatever
-  // the level.  Operator gamma*2 + delta.
-  const int q = p - 1;
-  std::vector<double> T((size_t)4 * p * p * 2, 0.0);
-  std::vector<double> w((size_t)2 * p);
-  for (int gamma = 0; gamma < 2; ++gamma) {
-    for (int delta = 0; delta < 2; ++delta) {
-      const int op = gamma * 2 + delta;
-      for (int l = 0; l < p; ++l) {
-        const double tau = (double)(delta * q + l) / (2.0 * q);
-        leaf_weights(p, tau, w.data());
-        // e^{2 pi i gamma tau_l} = e^{i pi gamma (delta q + l)/q}, an exact rational angle
-        const double ang = M_PI * (double)(gamma * (delta * q + l)) / q;
-        const double c = std::cos(ang), sn = std::sin(ang);
-        for (int m = 0; m < p; ++m) {
-          const double wr = w[2 * m], wi = w[2 * m + 1];
-          const double re = c * wr - sn * wi, im = c * wi + sn * wr;
-          const size_t at = adjoint ? (((size_t)op * p + l) * p + m) : (((size_t)op * p + m) * p + l);
-          T[2 * at] = re;
-          T[2 * at + 1] = adjoint ? -im : im;
-        }
-      }
-    }
-  }
-  return T;
-}
-
 namespace {
 
 // Per-unit program before slot numbering: tiles of every pass keyed by a D-bit mask whose

@@ -101,11 +101,7 @@ std::string build_tree(HostTree &T, int dim, int L, double N, double scale, int6
 // Transfer operators of the recursive step (eqs. M1 and E1 combined) for the rescaled
 // charges g^{AB}_m = e^{2 pi i a m/q} f^{AB}_m (a the index of A along the axis), per
 // axis:  C^{(gamma,delta)}[m][l] = w_m(tau_l) e^{2 pi i gamma tau_l},
-// tau_l = (delta + l/q)/2, gamma the bit of A within A', delta that of Bc within B;
-// stored [4][p][p] as interleaved (re, im) doubles, op index gamma*2 + delta.
-// adjoint = true stores the conjugate transpose of every operator.
-std::vector<double> transfer_table(int p, bool adjoint);
-
+// tau_l = (delta + l/q)/2, gamma the bit of A within A', delta that of Bc within B.
 // The factors of the transfer operators, C^{(gamma,delta)} = W(delta) diag(phi_gamma)
 // (phi_0 = 1), as interleaved (re, im) doubles: W [2][p][p] (delta, row, column) and
 // phi [2][p] = phi_1 for delta = 0, 1.  adjoint = true gives the factors of the

@@ -34,7 +34,7 @@ struct bfly_plan_s {
   int32_t *perm_x = nullptr, *perm_k = nullptr, *leaf_x = nullptr, *leaf_k = nullptr;
   int32_t *pleaf_x = nullptr, *pleaf_k = nullptr;
   double *off_x = nullptr, *off_k = nullptr, *xs = nullptr, *ks_ = nullptr, *inv_den = nullptr;
-  void *Wx = nullptr, *Wk = nullptr, *table = nullptr, *tableH = nullptr;
+  void *Wx = nullptr, *Wk = nullptr;
   struct DevProg {
     bfly::ChunkDesc *chunks = nullptr;
     unsigned char *blob = nullptr;
@@ -93,7 +93,6 @@ inline bfly::LevelArgs level_args(bfly_plan_t P, int s, bool adjoint, int nrhs) 
   a.nchunks = (int)pg.chunks.size();
   a.blob = dp.blob;
   a.runs = dp.runs;
-  a.table = adjoint ? P->tableH : P->table;
   a.cap0 = P->caps.cap0;
   a.cap1 = P->caps.cap1;
   a.meta_bytes = P->caps.meta_bytes;
