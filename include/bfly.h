@@ -60,6 +60,9 @@ typedef enum { BFLY_PREC_FP64 = 0, BFLY_PREC_FP32 = 1 } bfly_precision;
  * the fastest.  With tune_cache set, a choice recorded there for the same GPU, dim, p,
  * precision, nrhs and size class is reused, and new choices are appended. */
 #define BFLY_FLAG_AUTOTUNE 4u
+/* One stage per launch of the recursive step also in 2D (no stages fused in shared
+ * memory): the unfused programs of Sec. 2.2 step 3, for comparison and testing. */
+#define BFLY_FLAG_ONE_STAGE 8u
 
 typedef struct {
   int prec;                /* bfly_precision; default BFLY_PREC_FP32 */
@@ -246,6 +249,21 @@ bfly_status bfly_plan_info(bfly_plan_t plan, bfly_plan_info_t *info);
  * of range or a NULL pointer.
  */
 bfly_status bfly_plan_step(bfly_plan_t plan, int s, int *t, int *levels);
+
+/*
+ * bfly_plan_program — a copy of the compiled chunk program of recursive-step launch s
+ * (adjoint = 0: forward, 1: adjoint) for inspection and testing.  what = 0: the chunk
+ * descriptors (32 bytes each: blob offset and bytes, first run and run count, input
+ * tiles, passes, 2 padding), 1: the metadata blobs (per chunk: a 64-byte header {passes,
+ * inputs, output runs, 0, items of passes 0..5, two-source items of passes 0..5}, the
+ * items of every pass (8 bytes: source slots 0 and 1 (0xffff: none), destination slot,
+ * operators gamma*2 + delta of source 0 in bits 0-1 and of source 1 in bits 2-3), the
+ * output runs), 2: the input runs (8 bytes each: first global tile, first slot, count).
+ * out = NULL: *bytes receives the size; else min(size, cap) bytes are copied to out and
+ * *bytes receives the size.  Works for host-only plans.
+ */
+bfly_status bfly_plan_program(bfly_plan_t plan, int s, int adjoint, int what, void *out, int64_t cap,
+                              int64_t *bytes);
 
 /* Stage t (0..L): number of non-empty T_X boxes at level L-t (nA) and T_K boxes at
  * level t (nB); the stage holds nA*nB equivalent-charge tiles. */

@@ -255,7 +255,7 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     return bfly::StageTrees{&P->TX.cs[L - t - 1], &P->TX.idx[L - t], &P->TK.cs[t], &P->TK.idx[t + 1]};
   };
   std::deque<int> todo;
-  if (dim == 3) {
+  if (dim == 3 || (o.flags & BFLY_FLAG_ONE_STAGE)) {
     todo.assign(L, 1);
   } else {
     if (L % bfly::kMaxLevels) todo.push_back(L % bfly::kMaxLevels);
@@ -551,6 +551,22 @@ bfly_status bfly_plan_step(bfly_plan_t plan, int s, int *t, int *levels) {
   if (s < 0 || s >= (int)plan->steps.size()) return fail(BFLY_ERR_INVALID_ARG, "step outside 0..steps-1");
   *t = plan->steps[s].t;
   *levels = plan->steps[s].levels;
+  return BFLY_OK;
+}
+
+bfly_status bfly_plan_program(bfly_plan_t plan, int s, int adjoint, int what, void *out, int64_t cap,
+                              int64_t *bytes) {
+  if (!plan || !bytes) return fail(BFLY_ERR_INVALID_ARG, "NULL argument");
+  if (s < 0 || s >= (int)plan->steps.size()) return fail(BFLY_ERR_INVALID_ARG, "step outside 0..steps-1");
+  if (what < 0 || what > 2) return fail(BFLY_ERR_INVALID_ARG, "what must be 0, 1 or 2");
+  const bfly::StageProgram &pg = adjoint ? plan->progA[s] : plan->progF[s];
+  const void *src = what == 0 ? (const void *)pg.chunks.data() : what == 1 ? (const void *)pg.blob.data()
+                                                                            : (const void *)pg.runs.data();
+  const int64_t n = what == 0 ? (int64_t)(pg.chunks.size() * sizeof(bfly::ChunkDesc))
+                    : what == 1 ? (int64_t)pg.blob.size()
+                                : (int64_t)(pg.runs.size() * sizeof(bfly::Run));
+  *bytes = n;
+  if (out && cap > 0 && n > 0) std::memcpy(out, src, (size_t)std::min(n, cap));
   return BFLY_OK;
 }
 

@@ -15,6 +15,7 @@ BFLY_PREC_FP64, BFLY_PREC_FP32 = 0, 1
 BFLY_FLAG_HOST_ONLY = 1
 BFLY_FLAG_TEST_STALL = 2
 BFLY_FLAG_AUTOTUNE = 4
+BFLY_FLAG_ONE_STAGE = 8
 
 # Every function the header declares, with (restype, argtypes).
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -58,6 +59,7 @@ SIGNATURES = {
     "bfly_device_status": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "bfly_plan_stage": (_i, [_vp, _i, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "bfly_plan_step": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "bfly_plan_program": (_i, [_vp, _i, _i, _i, _vp, _i64, ctypes.POINTER(_i64)]),
     "bfly_last_error": (ctypes.c_char_p, []),
     "bfly_version": (ctypes.c_char_p, []),
 }

@@ -114,6 +114,21 @@ class Plan:
             out.append((t.value, lev.value))
         return out
 
+    def program(self, s: int, adjoint: bool = False) -> dict:
+        """bfly_plan_program: the chunk program of recursive-step launch s as numpy arrays
+        {"chunks": int32 [n][8], "blob": uint8 [bytes], "runs": uint8 [n_runs * 8]}."""
+        out = {}
+        for what, name in ((0, "chunks"), (1, "blob"), (2, "runs")):
+            n = ctypes.c_int64()
+            native.check(self._lib.bfly_plan_program(self._h, s, int(adjoint), what, None, 0, ctypes.byref(n)),
+                         "bfly_plan_program")
+            buf = np.zeros(n.value, dtype=np.uint8)
+            native.check(self._lib.bfly_plan_program(self._h, s, int(adjoint), what, buf.ctypes.data, n.value,
+                                                     ctypes.byref(n)), "bfly_plan_program")
+            out[name] = buf
+        out["chunks"] = out["chunks"].view(np.int32).reshape(-1, 8)
+        return out
+
     def stages(self) -> list:
         """[(t, nA, nB)] for t = 0..L: stage t pairs nA T_X boxes with nB T_K boxes."""
         out = []
