@@ -217,7 +217,8 @@ bfly_status bfly_device_status(bfly_plan_t plan, int *flags);
  * Batches: many independent transforms (each the operation of bfly_execute, Sec. 2.2)
  * run together.  The paper has no counterpart; a batch groups plans of equal dim, p and
  * precision (different N and point sets), aligned at the final stage, and runs one
- * launch of the recursive step per stage over the work of every plan.
+ * launch of the recursive step per stage t over the work of every plan's launch that
+ * starts at stage t (bfly_plan_step), the chunks of all plans scheduled together.
  *
  * bfly_batch_create — plans: count device plans (the caller keeps ownership and must
  *   keep them alive while the batch exists).  The plans must have been created with the

@@ -208,7 +208,8 @@ class Plan:
 
 class Batch:
     """Many plans (same dim, p, precision) executed together: one launch of the recursive
-    step per stage over all of them, captured in a CUDA graph on a non-default stream."""
+    step per starting stage over all of them, captured in a CUDA graph on a non-default
+    stream."""
 
     def __init__(self, plans):
         self._lib = native.load()
