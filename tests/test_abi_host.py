@@ -142,3 +142,22 @@ def test_empty_sides_are_accepted(nx, nk):
                                 np.ascontiguousarray(k).ctypes.data, 5, ctypes.byref(o)) == (1 if nx > 0 else 0)
     if h.value:
         lib.bfly_plan_destroy(h)
+
+
+def test_program_export_sizes_and_errors():
+    inst = w.small_random(2, 256.0, 7, 300, 260, 11, edge_fraction=0.3)
+    P = Plan(inst.x, inst.k, 256.0, 7, host_only=True)
+    lib, n = P._lib, ctypes.c_int64()
+    for s in range(P.info()["steps"]):
+        for adj in (0, 1):
+            prog = P.program(s, bool(adj))
+            nch = prog["chunks"].shape[0]
+            assert nch >= 1 and prog["runs"].size % 8 == 0 and prog["blob"].size % 16 == 0
+            # a partial copy fills only cap bytes and still reports the whole size
+            buf = np.full(40, 0xAB, dtype=np.uint8)
+            assert lib.bfly_plan_program(P._h, s, adj, 0, buf.ctypes.data, 32, ctypes.byref(n)) == 0
+            assert n.value == nch * 32 and (buf[32:] == 0xAB).all()
+            assert (buf[:32].view(np.int32) == prog["chunks"][0]).all()
+    assert lib.bfly_plan_program(P._h, P.info()["steps"], 0, 0, None, 0, ctypes.byref(n)) == native.BFLY_ERR_INVALID_ARG
+    assert lib.bfly_plan_program(P._h, 0, 0, 3, None, 0, ctypes.byref(n)) == native.BFLY_ERR_INVALID_ARG
+    assert lib.bfly_plan_program(None, 0, 0, 0, None, 0, ctypes.byref(n)) == native.BFLY_ERR_INVALID_ARG
