@@ -35,7 +35,7 @@ typedef enum {
   BFLY_ERR_INVALID_ARG = 1,   /* bad dimension, p, N, point, pointer or size */
   BFLY_ERR_OUT_OF_MEMORY = 2, /* a host or device allocation failed */
   BFLY_ERR_CUDA = 3,          /* a CUDA runtime call or kernel launch failed */
-  BFLY_ERR_UNSUPPORTED = 4,   /* valid request outside what this build implements */
+  BFLY_ERR_UNSUPPORTED = 4,   /* valid request outside what the library implements */
   BFLY_ERR_TIMEOUT = 5        /* a bounded device-side wait gave up */
 } bfly_status;
 

@@ -120,7 +120,7 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   *out = nullptr;
   if (dim != 2 && dim != 3) return fail(BFLY_ERR_INVALID_ARG, "dim must be 2 or 3");
   if (p < 3 || p > 9) return fail(BFLY_ERR_INVALID_ARG, "p must be in 3..9");
-  if (p % 2 == 0) return fail(BFLY_ERR_UNSUPPORTED, "this build has kernels for p = 3, 5, 7, 9");
+  if (p % 2 == 0) return fail(BFLY_ERR_UNSUPPORTED, "the library has kernels for p = 3, 5, 7, 9");
   if (!std::isfinite(N) || !(N > 0)) return fail(BFLY_ERR_INVALID_ARG, "N must be finite and > 0");
   const int L = levels_for(N);
   if ((dim == 2 && L > 30) || (dim == 3 && L > 20))
