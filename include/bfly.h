@@ -266,6 +266,16 @@ bfly_status bfly_plan_step(bfly_plan_t plan, int s, int *t, int *levels);
 bfly_status bfly_plan_program(bfly_plan_t plan, int s, int adjoint, int what, void *out, int64_t cap,
                               int64_t *bytes);
 
+/*
+ * bfly_plan_boxes — the non-empty boxes of level lev (0 = root .. L) of T_X (side = 0) or
+ * T_K (side = 1) in the plan's order (Sec. 2.2 step 1; Morton order, children of a box
+ * consecutive): out[i][d] = integer index of box i along axis d.  A stage-t charge tile
+ * of the stage buffers is at iA * nB + iB with A the box of T_X level L - t and B that of
+ * T_K level t in this order.  out = NULL: *n receives the box count; else min(n, cap)
+ * boxes are copied.  Works for host-only plans.
+ */
+bfly_status bfly_plan_boxes(bfly_plan_t plan, int side, int lev, int32_t *out, int64_t cap, int64_t *n);
+
 /* Stage t (0..L): number of non-empty T_X boxes at level L-t (nA) and T_K boxes at
  * level t (nB); the stage holds nA*nB equivalent-charge tiles. */
 bfly_status bfly_plan_stage(bfly_plan_t plan, int t, int64_t *nA, int64_t *nB);

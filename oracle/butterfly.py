@@ -165,7 +165,7 @@ def _solve(xg, kg, N, U, dense):
     return U
 
 
-def _butterfly_one(x, k, f, N, p, dense, TX, TK, L, stats):
+def _butterfly_one(x, k, f, N, p, dense, TX, TK, L, stats, charges=None):
     dim = x.shape[1]
     q = p - 1
     tile = (p,) * dim
@@ -184,6 +184,8 @@ def _butterfly_one(x, k, f, N, p, dense, TX, TK, L, stats):
     F = F.reshape((1, nB) + tile)                  # F[iA, iB] at stage t = L
     if stats is not None:
         stats.append((L, 1, nB))
+    if charges is not None:
+        charges[L] = F.copy()
     # Step 3: t = L-1 .. 0, A at level L-t of T_X, B at level t of T_K.
     for t in range(L - 1, -1, -1):
         sA, sB = L - t, t
@@ -208,6 +210,8 @@ def _butterfly_one(x, k, f, N, p, dense, TX, TK, L, stats):
         F = Fn.reshape((nA, nBt) + tile)
         if stats is not None:
             stats.append((t, nA, nBt))
+        if charges is not None:
+            charges[t] = F.copy()
     # Step 4: targets of every leaf A of T_X from f^{A B0}.
     kg0 = TK.grid_1d(0, p)
     k0 = _grid_points(kg0)[0]                      # k^{B0}_l = l N/(p-1)
@@ -234,6 +238,21 @@ def butterfly(x, k, f, N, p, dense: bool = False, stats: list | None = None):
         return _butterfly_one(x, k, f, N, p, dense, TX, TK, L, stats)
     return np.stack([_butterfly_one(x, k, fr, N, p, dense, TX, TK, L, stats if r == 0 else None)
                      for r, fr in enumerate(f)])
+
+
+def stage_charges(x, k, f, N, p, dense: bool = False):
+    """The equivalent charges of every stage (Sec. 2.2 steps 2 and 3) for one right-hand
+    side: returns (TX, TK, L, {t: F_t}), F_t[iA, iB] the p^d tile f^{AB} of A = box iA of
+    TX.boxes[L - t] and B = box iB of TK.boxes[t] (the trees of the scaled points), the
+    tile's axis d the grid index along axis d."""
+    x = np.asarray(x, dtype=np.float64)
+    k = np.asarray(k, dtype=np.float64)
+    x, k, N = power_of_two_form(x, k, float(N))
+    L = levels_for(N)
+    TX, TK = Tree(x, N, L), Tree(k, N, L)
+    charges = {}
+    _butterfly_one(x, k, np.asarray(f, dtype=np.complex128), N, p, dense, TX, TK, L, None, charges)
+    return TX, TK, L, charges
 
 
 def butterfly_matrix(x, k, N, p, dense: bool = False):

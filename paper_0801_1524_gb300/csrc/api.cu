@@ -570,6 +570,15 @@ bfly_status bfly_plan_program(bfly_plan_t plan, int s, int adjoint, int what, vo
   return BFLY_OK;
 }
 
+bfly_status bfly_plan_boxes(bfly_plan_t plan, int side, int lev, int32_t *out, int64_t cap, int64_t *n) {
+  if (!plan || !n) return fail(BFLY_ERR_INVALID_ARG, "NULL argument");
+  if (side < 0 || side > 1 || lev < 0 || lev > plan->L) return fail(BFLY_ERR_INVALID_ARG, "side or level out of range");
+  const bfly::HostTree &T = side ? plan->TK : plan->TX;
+  *n = T.nbox(lev);
+  if (out && cap > 0) std::memcpy(out, T.idx[lev].data(), (size_t)std::min(*n, cap) * plan->dim * sizeof(int32_t));
+  return BFLY_OK;
+}
+
 bfly_status bfly_plan_stage(bfly_plan_t plan, int t, int64_t *nA, int64_t *nB) {
   if (!plan || !nA || !nB) return fail(BFLY_ERR_INVALID_ARG, "NULL argument");
   if (t < 0 || t > plan->L) return fail(BFLY_ERR_INVALID_ARG, "stage outside 0..L");

@@ -60,6 +60,7 @@ SIGNATURES = {
     "bfly_plan_stage": (_i, [_vp, _i, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "bfly_plan_step": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "bfly_plan_program": (_i, [_vp, _i, _i, _i, _vp, _i64, ctypes.POINTER(_i64)]),
+    "bfly_plan_boxes": (_i, [_vp, _i, _i, _vp, _i64, ctypes.POINTER(_i64)]),
     "bfly_last_error": (ctypes.c_char_p, []),
     "bfly_version": (ctypes.c_char_p, []),
 }

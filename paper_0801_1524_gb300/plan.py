@@ -129,6 +129,17 @@ class Plan:
         out["chunks"] = out["chunks"].view(np.int32).reshape(-1, 8)
         return out
 
+    def boxes(self, side: str, lev: int) -> np.ndarray:
+        """bfly_plan_boxes: int32 [n][dim] box indices of level `lev` of T_X (side "x") or
+        T_K (side "k") in the plan's (Morton) order."""
+        sd = {"x": 0, "k": 1}[side]
+        n = ctypes.c_int64()
+        native.check(self._lib.bfly_plan_boxes(self._h, sd, lev, None, 0, ctypes.byref(n)), "bfly_plan_boxes")
+        out = np.zeros((n.value, self.dim), dtype=np.int32)
+        native.check(self._lib.bfly_plan_boxes(self._h, sd, lev, out.ctypes.data, n.value, ctypes.byref(n)),
+                     "bfly_plan_boxes")
+        return out
+
     def stages(self) -> list:
         """[(t, nA, nB)] for t = 0..L: stage t pairs nA T_X boxes with nB T_K boxes."""
         out = []

@@ -10,6 +10,11 @@ them.  The operators are random matrices, so the checks hold for any operator va
   same stage-0 charges as the one-stage programs (BFLY_FLAG_ONE_STAGE) of the same points;
 * the adjoint programs are the adjoint: <F x, y> = <x, F^H y> with the conjugate-
   transposed operators, F the whole forward sweep of the recursive step.
+
+With the operators of the method (C^{(gamma,delta)} = W(delta) diag(phi_gamma) for the
+rescaled charges), the same programs carry the oracle's stage-L charges to its stage-0
+charges: the tile order, the child bits and the operator indices of the compiled
+programs agree with the oracle's Sec. 2.2 step 3.
 """
 import numpy as np
 import pytest
@@ -146,3 +151,95 @@ def test_planted_slot_error_is_caught():
     x = rng.standard_normal((n_in, 5, 5)) + 0j
     with pytest.raises(AssertionError):
         run_program(prog, 2, 5, x, {t: a * b for t, a, b in st}[t - lev + 1], _random_ops(rng, 5))
+
+
+# ---- the compiled programs with the operators of the method, against the oracle
+
+def _lagrange_w(p, tau):
+    """w(tau) = G^{-1} v(tau), G_{ll'} = e^{2 pi i l l'/q^2}, v(tau)_l = e^{2 pi i l tau/q}:
+    the weights that carry charges on a child grid to the parent grid (eq. M1)."""
+    q = p - 1
+    l = np.arange(p)
+    G = np.exp(2j * np.pi * np.outer(l, l) / q ** 2)
+    return np.linalg.solve(G, np.exp(2j * np.pi * l * tau / q))
+
+
+def _method_ops(p):
+    """C^{(gamma, delta)}[m][l] = w_m(tau_l) e^{2 pi i gamma tau_l}, tau_l = (delta + l/q)/2,
+    for the rescaled charges g_m = e^{2 pi i a m/q} f_m; op = gamma * 2 + delta."""
+    q = p - 1
+    ops = np.zeros((4, p, p), dtype=np.complex128)
+    for gamma in (0, 1):
+        for delta in (0, 1):
+            for l in range(p):
+                tau = (delta + l / q) / 2
+                ops[gamma * 2 + delta][:, l] = _lagrange_w(p, tau) * np.exp(2j * np.pi * gamma * tau)
+    return ops
+
+
+def _rescale(F, boxes, p):
+    """g^{AB}_m = prod_d e^{2 pi i a_d m_d / q} f^{AB}_m, a the index of A along each axis."""
+    q, dim = p - 1, boxes.shape[1]
+    G = F.astype(np.complex128).copy()
+    m = np.arange(p)
+    for d in range(dim):
+        ph = np.exp(2j * np.pi * np.outer(boxes[:, d], m) / q)  # [nA, p]
+        shape = [F.shape[0], 1] + [1] * dim
+        shape[2 + d] = p
+        G *= ph.reshape(shape)
+    return G
+
+
+def _to_plan_order(F, o_boxes_A, o_boxes_B, P, L, t):
+    """Oracle tiles F[iA, iB] (lexicographic boxes) -> the plan's tile order iA * nB + iB."""
+    pa, pb = P.boxes("x", L - t), P.boxes("k", t)
+    ia = {tuple(b): i for i, b in enumerate(o_boxes_A)}
+    ib = {tuple(b): i for i, b in enumerate(o_boxes_B)}
+    ra = np.array([ia[tuple(b)] for b in pa])
+    rb = np.array([ib[tuple(b)] for b in pb])
+    return F[ra][:, rb].reshape((len(pa) * len(pb),) + F.shape[2:])
+
+
+@pytest.mark.parametrize("dim,N,p,nx,nk,seed,flags", [
+    (2, 64.0, 5, 150, 120, 31, 0), (2, 200.0, 7, 260, 240, 32, 0), (2, 64.0, 5, 150, 120, 31, 8),
+    (3, 8.0, 3, 120, 100, 33, 0), (2, 0.75 * 128, 5, 160, 150, 34, 0)])
+def test_programs_reproduce_the_oracle_stage_charges(dim, N, p, nx, nk, seed, flags):
+    # stage L charges of the oracle (rescaled, in the plan's tile order) through every
+    # compiled launch with the operators of the method give the oracle's stage-0 charges
+    import oracle.butterfly as ob
+    inst = w.small_random(dim, N, p, nx, nk, seed, edge_fraction=0.3)
+    f = inst.sources()[0].astype(np.complex128)
+    TX, TK, L, F = ob.stage_charges(inst.x, inst.k, f, N, p)
+    P = Plan(inst.x, inst.k, N, p, host_only=True, flags=flags)
+    assert P.info()["L"] == L
+    gL = _to_plan_order(_rescale(F[L], TX.boxes[0], p), TX.boxes[0], TK.boxes[L], P, L, L)
+    g0 = sweep(P, gL, _method_ops(p))
+    ref = _to_plan_order(_rescale(F[0], TX.boxes[L], p), TX.boxes[L], TK.boxes[0], P, L, 0)
+    # the oracle's charges come from FP64 LU solves of the matching systems, each
+    # accurate to about cond(G)^dim * eps (G ill-conditioned: 4e2 at p = 5, 2e5 at
+    # p = 7); a wiring mistake in the programs would be of the charges' own size
+    q = p - 1
+    l = np.arange(p)
+    cond = np.linalg.cond(np.exp(2j * np.pi * np.outer(l, l) / q ** 2)) ** dim
+    err = np.abs(g0 - ref).max() / np.abs(ref).max()
+    assert err < 1e-9 + 20 * np.finfo(float).eps * cond, (err, cond)
+
+
+@pytest.mark.parametrize("mistake", ["gamma_delta_swapped", "operators_transposed", "charges_not_rescaled"])
+def test_planted_operator_mistakes_fail_the_oracle_check(mistake):
+    import oracle.butterfly as ob
+    inst = w.small_random(2, 64.0, 5, 150, 120, 31, edge_fraction=0.3)
+    f = inst.sources()[0].astype(np.complex128)
+    TX, TK, L, F = ob.stage_charges(inst.x, inst.k, f, 64.0, 5)
+    P = Plan(inst.x, inst.k, 64.0, 5, host_only=True)
+    ops = _method_ops(5)
+    gL = _to_plan_order(_rescale(F[L], TX.boxes[0], 5), TX.boxes[0], TK.boxes[L], P, L, L)
+    ref = _to_plan_order(_rescale(F[0], TX.boxes[L], 5), TX.boxes[L], TK.boxes[0], P, L, 0)
+    if mistake == "gamma_delta_swapped":
+        ops = ops[[0, 2, 1, 3]]
+    elif mistake == "operators_transposed":
+        ops = np.transpose(ops, (0, 2, 1))
+    else:
+        ref = _to_plan_order(F[0].astype(np.complex128), TX.boxes[L], TK.boxes[0], P, L, 0)
+    g0 = sweep(P, gL, ops)
+    assert np.abs(g0 - ref).max() / np.abs(ref).max() > 0.1
