@@ -1,6 +1,7 @@
 // C ABI of the butterfly (include/bfly.h): plan creation, upload and the execution entry
 // points.  Every step of the transform runs in the kernels of this library.
 #include <algorithm>
+#include <atomic>
 #include <deque>
 #include <chrono>
 #include <cstdlib>
@@ -9,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/bfly.h"
@@ -261,6 +263,58 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     if (L % bfly::kMaxLevels) todo.push_back(L % bfly::kMaxLevels);
     for (int i = 0; i < L / bfly::kMaxLevels; ++i) todo.push_back(bfly::kMaxLevels);
   }
+  // the programs of the planned steps, forward and adjoint, compiled on all host cores
+  // (each is independent); a step split after a capacity failure is compiled below
+  struct Compiled {
+    bfly::StageProgram prog;
+    bool fits = true, used = false;
+  };
+  std::vector<std::pair<int, int>> groups;  // (t, levels)
+  {
+    int t = L - 1;
+    for (int lev : todo) {
+      groups.push_back({t, lev});
+      t -= lev;
+    }
+  }
+  std::vector<Compiled> pre(groups.size() * 2);
+  std::atomic<bool> compile_failed{false};
+  {
+    std::atomic<size_t> next{0};
+    auto worker = [&]() {
+      for (size_t i; (i = next++) < pre.size();) {
+        try {
+          const int t = groups[i / 2].first, lev = groups[i / 2].second;
+          bfly::StageTrees st[bfly::kMaxLevels];
+          for (int l = 0; l < lev; ++l) st[l] = trees(t - l);
+          pre[i].prog = bfly::make_step_program(dim, p, st, lev, (i & 1) != 0, caps, &pre[i].fits);
+        } catch (...) {
+          compile_failed = true;
+        }
+      }
+    };
+    const size_t n_threads = std::min<size_t>(std::max(1u, std::thread::hardware_concurrency()), pre.size());
+    std::vector<std::thread> threads;
+    for (size_t i = 1; i < n_threads; ++i) threads.emplace_back(worker);
+    worker();
+    for (auto &th : threads) th.join();
+  }
+  if (compile_failed) {
+    delete P;
+    return fail(BFLY_ERR_OUT_OF_MEMORY, "host memory exhausted while compiling the stage programs");
+  }
+  auto compile = [&](int t, int lev, bool adjoint, bool *fits) {
+    for (size_t g = 0; g < groups.size(); ++g)
+      if (groups[g].first == t && groups[g].second == lev && !pre[2 * g + adjoint].used) {
+        Compiled &c = pre[2 * g + adjoint];
+        c.used = true;
+        *fits = c.fits;
+        return std::move(c.prog);
+      }
+    bfly::StageTrees st[bfly::kMaxLevels];
+    for (int l = 0; l < lev; ++l) st[l] = trees(t - l);
+    return bfly::make_step_program(dim, p, st, lev, adjoint, caps, fits);
+  };
   std::vector<bfly_plan_s::Step> plan_steps;
   int64_t lanes_used_all = 0, lanes_issued_all = 0;
   for (int t = L - 1; !todo.empty();) {
@@ -268,11 +322,9 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     todo.pop_front();
     bfly::StageProgram pf, pa;
     for (;;) {
-      bfly::StageTrees st[bfly::kMaxLevels];
-      for (int l = 0; l < lev; ++l) st[l] = trees(t - l);
       bool fits_f = true, fits_a = true;
-      pf = bfly::make_step_program(dim, p, st, lev, false, caps, &fits_f);
-      pa = bfly::make_step_program(dim, p, st, lev, true, caps, &fits_a);
+      pf = compile(t, lev, false, &fits_f);
+      pa = compile(t, lev, true, &fits_a);
       if ((fits_f && fits_a) || lev == 1) break;
       --lev;
       todo.push_front(1);
