@@ -187,10 +187,12 @@ bfly_status bfly_execute_events(bfly_plan_t plan, const void *in, void *out, int
  * bfly_execute_noalloc — bfly_execute (forward, device buffers) without any allocation:
  * the two charge buffers of the sweep come from a static device array owned by the
  * library (64 MiB in all, 32 MiB per buffer) instead of the plan's workspace.  The paper
- * has no counterpart; this entry point serves callers that cannot allocate device memory
- * when they run the transform (inside a CUDA graph capture, where cudaMalloc is not
- * allowed; under an external allocator or memory budget; or many plans sharing one fixed
- * workspace).  The plan itself must have been created beforehand.
+ * has no counterpart.  It serves callers that cannot allocate device memory at the time
+ * they run the transform: code whose device memory is owned by an external allocator or
+ * a fixed memory budget (a framework's caching allocator, a service with a preset
+ * footprint), code that must not call cudaMalloc on its execution path (cudaMalloc may
+ * synchronise the device and its latency is unbounded), and many plans that share one
+ * fixed workspace.  The plan itself must have been created beforehand.
  *   - Sizes: max_pairs * tile * element bytes * nrhs must fit in 32 MiB, otherwise the call
  *     returns BFLY_ERR_INVALID_ARG and says so; nothing is launched then.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
@@ -212,6 +214,25 @@ bfly_status bfly_execute_noalloc(bfly_plan_t plan, const void *f, void *u, int n
  * the bits.  Returns BFLY_ERR_TIMEOUT when any bit was set, else BFLY_OK.
  */
 bfly_status bfly_device_status(bfly_plan_t plan, int *flags);
+
+/*
+ * bfly_stream_status — bfly_device_status ordered on one stream: reads the plan's status
+ * word after the work already issued to `stream` (NULL: the legacy default stream) and
+ * clears it there, waiting for that stream only (work on other streams keeps running).
+ * *flags (optional) receives the bits.  Returns BFLY_ERR_TIMEOUT when any bit was set.
+ */
+bfly_status bfly_stream_status(bfly_plan_t plan, void *stream, int *flags);
+
+/*
+ * bfly_measure_peak — arithmetic throughput of the current device's SMs, the denominator
+ * of the roofline fraction of the recursive step (the paper has no counterpart): a
+ * register-resident loop of independent multiply-add chains on every SM, timed with CUDA
+ * events (best of three launches after a warm-up, on a stream of its own; synchronises
+ * that stream).  kind 0: FP64 fma; 1: FP32 fma; 2: paired FP32 fma (fma.rn.f32x2, the
+ * form of the FP32 recursive step).  *flops_per_s receives 2 flops per multiply-add;
+ * *ms (optional) the time of the best launch.  Allocates nothing.
+ */
+bfly_status bfly_measure_peak(int kind, double *flops_per_s, double *ms);
 
 /*
  * Batches: many independent transforms (each the operation of bfly_execute, Sec. 2.2)

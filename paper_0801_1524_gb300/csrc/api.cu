@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <thread>
@@ -278,7 +279,9 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     }
   }
   std::vector<Compiled> pre(groups.size() * 2);
-  std::atomic<bool> compile_failed{false};
+  std::atomic<int> compile_failed{0};  // 1: host memory exhausted, 2: another exception
+  std::string compile_error;
+  std::mutex compile_error_mutex;
   {
     std::atomic<size_t> next{0};
     auto worker = [&]() {
@@ -288,20 +291,35 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
           bfly::StageTrees st[bfly::kMaxLevels];
           for (int l = 0; l < lev; ++l) st[l] = trees(t - l);
           pre[i].prog = bfly::make_step_program(dim, p, st, lev, (i & 1) != 0, caps, &pre[i].fits);
+        } catch (const std::bad_alloc &) {
+          compile_failed = 1;
+        } catch (const std::exception &ex) {
+          std::lock_guard<std::mutex> lock(compile_error_mutex);
+          compile_failed = 2;
+          compile_error = ex.what();
         } catch (...) {
-          compile_failed = true;
+          compile_failed = 2;
         }
       }
     };
     const size_t n_threads = std::min<size_t>(std::max(1u, std::thread::hardware_concurrency()), pre.size());
     std::vector<std::thread> threads;
-    for (size_t i = 1; i < n_threads; ++i) threads.emplace_back(worker);
+    // threads that cannot be started leave their share to the others (the calling thread
+    // at least)
+    for (size_t i = 1; i < n_threads; ++i) {
+      try {
+        threads.emplace_back(worker);
+      } catch (...) {
+        break;
+      }
+    }
     worker();
     for (auto &th : threads) th.join();
   }
   if (compile_failed) {
     delete P;
-    return fail(BFLY_ERR_OUT_OF_MEMORY, "host memory exhausted while compiling the stage programs");
+    if (compile_failed == 1) return fail(BFLY_ERR_OUT_OF_MEMORY, "host memory exhausted while compiling the stage programs");
+    return fail(BFLY_ERR_CUDA, "internal error while compiling the stage programs: " + compile_error);
   }
   auto compile = [&](int t, int lev, bool adjoint, bool *fits) {
     for (size_t g = 0; g < groups.size(); ++g)
@@ -587,6 +605,20 @@ bfly_status bfly_device_status(bfly_plan_t plan, int *flags) {
   BFLY_CUDA(cudaDeviceSynchronize());
   BFLY_CUDA(cudaMemcpy(&v, plan->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (v) BFLY_CUDA(cudaMemset(plan->status, 0, sizeof(int)));
+  if (flags) *flags = v;
+  if (v) return fail(BFLY_ERR_TIMEOUT, "a bounded device-side wait gave up (status bits " + std::to_string(v) + ")");
+  return BFLY_OK;
+}
+
+bfly_status bfly_stream_status(bfly_plan_t plan, void *stream, int *flags) {
+  g_err.clear();
+  if (!plan || !plan->status) return fail(BFLY_ERR_INVALID_ARG, "plan is NULL or host-only");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int v = 0;
+  // a copy to pageable memory returns once it has completed, after the stream's earlier work
+  BFLY_CUDA(cudaMemcpyAsync(&v, plan->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BFLY_CUDA(cudaStreamSynchronize(s));
+  if (v) BFLY_CUDA(cudaMemsetAsync(plan->status, 0, sizeof(int), s));
   if (flags) *flags = v;
   if (v) return fail(BFLY_ERR_TIMEOUT, "a bounded device-side wait gave up (status bits " + std::to_string(v) + ")");
   return BFLY_OK;

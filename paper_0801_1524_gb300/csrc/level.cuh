@@ -437,7 +437,15 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
       const int64_t irhs = a.entries ? a.entries[ch].in_rhs : a.in_rhs;
       slot_it[s] = it;
       slot_w[s] = w;
-      if (a.inject_stall && it == 0) continue;  // test hook: the first chunk never arrives
+      if (a.inject_stall && it == 0) {
+        // test hook: the first chunk never arrives (every later copy still follows the
+        // predecessor grid, as in a normal launch)
+        if (!waited) {
+          pdl_wait();
+          waited = true;
+        }
+        continue;
+      }
       unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
       unsigned char *in_s = reinterpret_cast<unsigned char *>(slot0 + (size_t)s * a.cap0 * TS);
       if (lane == 0) {

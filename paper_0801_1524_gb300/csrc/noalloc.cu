@@ -2,10 +2,11 @@
 // buffers (the sweep's scratch memory) taken from a fixed, statically allocated device
 // array instead of the plan's workspace, so that the call allocates nothing.
 //
-// For callers that cannot allocate device memory when they run the transform: code
-// running under a CUDA graph capture (where cudaMalloc is not allowed), code driven by an
-// external allocator or memory budget that forbids allocations, and code that runs many
-// plans and wants them to share one fixed workspace instead of one workspace per plan.
+// For callers that cannot allocate device memory when they run the transform: code whose
+// device memory belongs to an external allocator or a fixed memory budget, code that must
+// not call cudaMalloc on its execution path (it may synchronise the device, and its
+// latency is unbounded), and code that runs many plans and wants them to share one fixed
+// workspace instead of one workspace per plan.
 //
 // The array below is a file-scope __device__ variable: every GPU that loads the library
 // holds it until the process exits.  In host code its name is only a stand-in for the

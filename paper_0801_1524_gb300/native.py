@@ -57,6 +57,8 @@ SIGNATURES = {
     "bfly_batch_status": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "bfly_batch_destroy": (None, [_vp]),
     "bfly_device_status": (_i, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "bfly_stream_status": (_i, [_vp, _vp, ctypes.POINTER(ctypes.c_int)]),
+    "bfly_measure_peak": (_i, [_i, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "bfly_plan_stage": (_i, [_vp, _i, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "bfly_plan_step": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "bfly_plan_program": (_i, [_vp, _i, _i, _i, _vp, _i64, ctypes.POINTER(_i64)]),

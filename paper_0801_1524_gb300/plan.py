@@ -99,6 +99,15 @@ class Plan:
             native.check(st, "bfly_device_status")
         return flags.value
 
+    def stream_status(self, stream=None) -> int:
+        """bfly_stream_status: the status word read and cleared in the order of `stream`
+        (default: the current stream), waiting for that stream only."""
+        flags = ctypes.c_int(0)
+        st = self._lib.bfly_stream_status(self._h, _stream_ptr(stream), ctypes.byref(flags))
+        if st not in (native.BFLY_OK, 5):
+            native.check(st, "bfly_stream_status")
+        return flags.value
+
     def info(self) -> dict:
         inf = native.PlanInfo()
         native.check(self._lib.bfly_plan_info(self._h, ctypes.byref(inf)), "bfly_plan_info")
@@ -178,8 +187,10 @@ class Plan:
         return self._run(self._lib.bfly_execute, f, self.nk, self.nx, out, stream, "bfly_execute")
 
     def forward_noalloc(self, f, out=None, stream=None):
-        """bfly_execute_noalloc: the forward transform with the library's static workspace
-        (for callers that cannot allocate device memory at that point; see bfly.h)."""
+        """bfly_execute_noalloc: the forward transform with the library's static workspace,
+        for callers that cannot allocate device memory when they run it (an external
+        allocator or fixed memory budget owns the device memory, or cudaMalloc's device
+        synchronisation is not acceptable on their execution path)."""
         return self._run(self._lib.bfly_execute_noalloc, f, self.nk, self.nx, out, stream,
                          "bfly_execute_noalloc")
 
@@ -266,6 +277,16 @@ class Batch:
         if st not in (native.BFLY_OK, 5):
             native.check(st, "bfly_batch_status")
         return flags.value
+
+
+def measure_peak(kind: str) -> float:
+    """bfly_measure_peak on the current device: flop/s of "fp64" (fma), "fp32" (fma) or
+    "fp32x2" (paired fma.rn.f32x2) multiply-add loops on every SM."""
+    code = {"fp64": 0, "fp32": 1, "fp32x2": 2}[kind]
+    lib = native.load()
+    v, ms = ctypes.c_double(), ctypes.c_double()
+    native.check(lib.bfly_measure_peak(code, ctypes.byref(v), ctypes.byref(ms)), "bfly_measure_peak")
+    return v.value
 
 
 def butterfly_fn():

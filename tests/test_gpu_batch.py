@@ -60,3 +60,39 @@ def test_batch_rejects_mixed_plans():
     b = w.small_random(2, 64.0, 5, 100, 100, 2)
     with pytest.raises(BflyError):
         Batch([Plan(a.x, a.k, a.N, 7), Plan(b.x, b.k, b.N, 5)])
+
+
+@pytest.mark.slow
+def test_star_batch_full_size():
+    # the batched workload as the benchmark runs it: 64 star-curve instances, N drawn
+    # log-uniformly in [512, 16384] (not powers of two), p = 7, 16 complex64 right-hand
+    # sides each, graph replay on a side stream
+    from paper_0801_1524_gb300.plan import Batch, Plan
+    insts = w.star_batch(nrhs=16)
+    out = {}
+    for prec, dtype in (("fp32", torch.complex64), ("fp64", torch.complex128)):
+        plans = [Plan(I.x, I.k, I.N, I.p, precision=prec, max_nrhs=16) for I in insts]
+        batch = Batch(plans)
+        fs = [torch.as_tensor(I.sources(), device="cuda").to(dtype) for I in insts]
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            us = [torch.empty((16, I.x.shape[0]), dtype=dtype, device="cuda") for I in insts]
+            for _ in range(2):  # capture, then a replay
+                batch.forward(fs, us, stream=side)
+        side.synchronize()
+        assert batch.device_status() == 0
+        if prec == "fp32":
+            # every instance equals its own plan's transform (the same chunk arithmetic)
+            for P, f, u in zip(plans, fs, us):
+                assert torch.equal(u, P.forward(f))
+        out[prec] = [u.to(torch.complex128).cpu().numpy() for u in us]
+        del batch, plans
+    # FP32 against FP64 on every instance and right-hand side
+    worst = max(rel_l2(a[r], b[r]) for a, b in zip(out["fp32"], out["fp64"]) for r in range(16))
+    assert worst < 1e-6, worst
+    # the two smallest instances against the oracle's butterfly, all 16 right-hand sides
+    for i in sorted(range(len(insts)), key=lambda i: insts[i].N)[:2]:
+        I = insts[i]
+        ref = ob.butterfly(I.x, I.k, I.sources(), I.N, I.p)
+        assert rel_l2(out["fp64"][i], ref) < 1e-9
+        assert rel_l2(out["fp32"][i], ref) < 1e-6

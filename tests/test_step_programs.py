@@ -243,3 +243,54 @@ def test_planted_operator_mistakes_fail_the_oracle_check(mistake):
         ref = _to_plan_order(F[0].astype(np.complex128), TX.boxes[L], TK.boxes[0], P, L, 0)
     g0 = sweep(P, gL, ops)
     assert np.abs(g0 - ref).max() / np.abs(ref).max() > 0.1
+
+
+def _pairwise_sweep(TX, TK, L, gL, ops, dim):
+    """The recursive step pair by pair on the oracle's trees (no programs, no fusion, no
+    sum factorisation): g^{AB} = sum_c (x)_d C^{(gamma_d(A), delta_d(Bc))} g^{A'Bc} for
+    every stage t = L-1 .. 0, tiles indexed [iA, iB] in the oracle's box order."""
+    g = gL
+    for t in range(L - 1, -1, -1):
+        A, Ap, B, Bc = TX.boxes[L - t], TX.boxes[L - t - 1], TK.boxes[t], TK.boxes[t + 1]
+        ia = {tuple(b): i for i, b in enumerate(Ap)}
+        ib = {tuple(b): i for i, b in enumerate(B)}
+        kids = {}
+        for j, c in enumerate(Bc):
+            kids.setdefault(ib[tuple(c // 2)], []).append(j)
+        out = np.zeros((len(A), len(B)) + g.shape[2:], dtype=np.complex128)
+        for i, a in enumerate(A):
+            ip = ia[tuple(a // 2)]
+            for jb, js in kids.items():
+                for jc in js:
+                    y = g[ip, jc]
+                    for d in range(dim):
+                        y = _apply(ops[(a[d] & 1) * 2 + (Bc[jc][d] & 1)], y, d)
+                    out[i, jb] += y
+        g = out
+    return g
+
+
+@pytest.mark.parametrize("dim,N,p,nx,nk,seed,flags", [
+    (2, 200.0, 7, 260, 240, 32, 0), (2, 128.0, 9, 200, 180, 35, 0), (2, 200.0, 7, 260, 240, 32, 8),
+    (3, 8.0, 5, 120, 100, 36, 0), (2, 0.75 * 128, 7, 160, 150, 34, 0)])
+def test_programs_equal_the_pairwise_recursion(dim, N, p, nx, nk, seed, flags):
+    # the same operators of the method on both sides, so that the conditioning of the
+    # matching systems drops out: the compiled (fused, sum-factorised) programs must give
+    # the pairwise recursion's stage-0 charges to rounding, and a 1e-6 change of one
+    # operator must be seen
+    import oracle.butterfly as ob
+    inst = w.small_random(dim, N, p, nx, nk, seed, edge_fraction=0.3)
+    f = inst.sources()[0].astype(np.complex128)
+    TX, TK, L, F = ob.stage_charges(inst.x, inst.k, f, N, p)
+    P = Plan(inst.x, inst.k, N, p, host_only=True, flags=flags)
+    ops = _method_ops(p)
+    gL_o = _rescale(F[L], TX.boxes[0], p)
+    ref = _to_plan_order(_pairwise_sweep(TX, TK, L, gL_o, ops, dim), TX.boxes[L], TK.boxes[0], P, L, 0)
+    gL = _to_plan_order(gL_o, TX.boxes[0], TK.boxes[L], P, L, L)
+    scale = np.abs(ref).max()
+    err = np.abs(sweep(P, gL, ops) - ref).max() / scale
+    assert err < 1e-12, err
+    planted = ops.copy()
+    planted[3] *= 1.0 + 1e-6
+    err_planted = np.abs(sweep(P, gL, planted) - ref).max() / scale
+    assert err_planted > 1e-8, err_planted
