@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--smem-kb", type=int, default=0,
                     help="shared memory per block of the recursive step (0 = the library default)")
+    ap.add_argument("--precision", default="fp32",
+                    help="star_batch: comma-separated precisions of the batch (fp32, tc); the first is the value")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and p = 9 companion measurements of the default run")
     return ap.parse_args()
@@ -420,8 +422,11 @@ def main_bfly(args, rank, world, dist):
     if not args.no_extras and world == 1:
         del u
         torch.cuda.empty_cache()
-        line["star_batch"] = batch_summary(args, dev, flush)
-        line["p9_rows"] = p9_rows(dev)
+        for key, fn in (("star_batch", lambda: batch_summary(args, dev, flush)), ("p9_rows", lambda: p9_rows(dev))):
+            try:
+                line[key] = fn()
+            except Exception as exc:  # recorded in the line; the headline stands
+                line[key] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_baselines:
         rate, m, thr, dt = oracle_direct_rate(inst, f_np.astype(np.complex128), args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "transforms/s", "cores": thr, "kind": "oracle",
@@ -496,20 +501,25 @@ def main_reference(args, rank):
             "wall_s": wall, "targets_per_step": m}
 
 
-def run_batch(insts, nrhs, steps32, steps64, warmup, dev, flush, smem_kb=0, precision32="fp32"):
+def run_batch(insts, nrhs, steps32, steps64, warmup, dev, flush, smem_kb=0, precisions=("fp32",), stages=0):
     """The batched sweep of `insts` (nrhs complex64 right-hand sides each; one recursive-step
-    launch per starting stage over all instances, graph replay on a side stream) in FP32
-    and FP64; CUDA events around every replay, L2 flushed between replays."""
+    launch per starting stage over all instances, graph replay on a side stream) in each of
+    `precisions` ("fp32": paired FP32 multiply-adds; "tc": tensor cores) and in FP64; CUDA
+    events around every replay, L2 flushed between replays.  Returns, per precision, the
+    time per batch and its accuracy against the FP64 batch."""
     import torch
     from paper_0801_1524_gb300.plan import Batch, Plan
     out = {}
-    for prec, dtype, steps in ((precision32, torch.complex64, steps32), ("fp64", torch.complex128, steps64)):
+    runs = [(pr, torch.complex64, steps32) for pr in precisions] + [("fp64", torch.complex128, steps64)]
+    for prec, dtype, steps in runs:
         plans = [Plan(I.x, I.k, I.N, I.p, precision=prec, max_nrhs=nrhs,
-                      smem_kb=smem_kb if prec != "fp64" else 0) for I in insts]
+                      smem_kb=smem_kb if prec != "fp64" else 0, stages=stages if prec != "fp64" else 0)
+                 for I in insts]
         batch = Batch(plans)
         fs = [torch.as_tensor(I.sources(dtype=np.complex64, nrhs=nrhs), device=dev).to(dtype) for I in insts]
         us = [torch.empty((nrhs, I.x.shape[0]), dtype=dtype, device=dev) for I in insts]
         side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
             for _ in range(max(warmup, 1)):
                 batch.forward(fs, us, stream=side)
@@ -525,21 +535,27 @@ def run_batch(insts, nrhs, steps32, steps64, warmup, dev, flush, smem_kb=0, prec
         out[prec] = {"ms": float(np.mean([a.elapsed_time(b) for a, b in evs])),
                      "us": [u.to(torch.complex128) for u in us], "status": batch.device_status(),
                      "flops": sum(p.info()["flops_fwd"] for p in plans) * nrhs,
-                     "alg_flops": sum(p.info()["jobs_fwd"] for p in plans) * 2 * insts[0].p ** 3 * 8.0 * nrhs}
+                     "alg_flops": sum(p.info()["jobs_fwd"] for p in plans) * 2 * insts[0].p ** 3 * 8.0 * nrhs,
+                     "smem_kb": plans[0].info()["smem_kb"], "steps": steps,
+                     "stages_per_launch": plans[0].info()["stages_per_launch"]}
         del batch, plans, fs, us
-    u32, u64 = out[precision32]["us"], out["fp64"]["us"]
-    num = sum(torch.linalg.norm(a - b).item() ** 2 for a, b in zip(u32, u64))
-    den = sum(torch.linalg.norm(b).item() ** 2 for b in u64)
-    worst = max((torch.linalg.norm(a[r] - b[r]) / torch.linalg.norm(b[r])).item()
-                for a, b in zip(u32, u64) for r in range(a.shape[0]))
-    ms = out[precision32]["ms"]
-    return {"ms": ms, "fp64_batch_ms": out["fp64"]["ms"], "speedup_vs_fp64": out["fp64"]["ms"] / ms,
-            "rel_l2_fp32_vs_fp64": (num / den) ** 0.5, "worst_instance_rhs_rel_l2": worst,
-            "gate_1e-6_met": (num / den) ** 0.5 <= 1e-6,
-            "recursive_executed_tflops": out[precision32]["flops"] / (ms * 1e-3) / 1e12,
-            "recursive_alg_tflops": out[precision32]["alg_flops"] / (ms * 1e-3) / 1e12,
-            "status": [out[precision32]["status"], out["fp64"]["status"]],
-            "steps": [steps32, steps64]}
+    u64 = out["fp64"]["us"]
+    res = {"fp64_batch_ms": out["fp64"]["ms"], "fp64_status": out["fp64"]["status"]}
+    for prec in precisions:
+        o = out[prec]
+        num = sum(torch.linalg.norm(a - b).item() ** 2 for a, b in zip(o["us"], u64))
+        den = sum(torch.linalg.norm(b).item() ** 2 for b in u64)
+        worst = max((torch.linalg.norm(a[r] - b[r]) / torch.linalg.norm(b[r])).item()
+                    for a, b in zip(o["us"], u64) for r in range(a.shape[0]))
+        ms = o["ms"]
+        res[prec] = {"ms": ms, "speedup_vs_fp64": out["fp64"]["ms"] / ms,
+                     "rel_l2_vs_fp64": (num / den) ** 0.5, "worst_instance_rhs_rel_l2": worst,
+                     "gate_1e-6_met": (num / den) ** 0.5 <= 1e-6,
+                     "recursive_executed_tflops": o["flops"] / (ms * 1e-3) / 1e12,
+                     "recursive_alg_tflops": o["alg_flops"] / (ms * 1e-3) / 1e12,
+                     "status": o["status"], "smem_kb": o["smem_kb"], "steps": o["steps"],
+                     "stages_per_launch": o["stages_per_launch"]}
+    return res
 
 
 def batch_summary(args, dev, flush):
@@ -547,10 +563,12 @@ def batch_summary(args, dev, flush):
     (N log-uniform in [512, 16384], as drawn), p = 7, 16 complex64 right-hand sides each."""
     from paper_0801_1524_gb300 import workloads as w
     insts = w.star_batch(nrhs=16)
-    r = run_batch(insts, 16, steps32=10, steps64=2, warmup=2, dev=dev, flush=flush)
+    r = run_batch(insts, 16, steps32=10, steps64=2, warmup=2, dev=dev, flush=flush, precisions=("fp32", "tc"))
     r["workload"] = ("star_batch: 64 instances, N log-uniform in 512..16384 (sum N = %.0f), p=7, "
-                     "16 complex64 RHS each, graph replay, FP32 vs FP64 batch" % sum(I.N for I in insts))
-    r["instance_rhs_per_s"] = len(insts) * 16 * 1e3 / r["ms"]
+                     "16 complex64 RHS each, graph replay; FP32 (paired FP32 multiply-adds) and TC "
+                     "(tensor cores, 3xTF32) batches against the FP64 batch" % sum(I.N for I in insts))
+    for prec in ("fp32", "tc"):
+        r[prec]["instance_rhs_per_s"] = len(insts) * 16 * 1e3 / r[prec]["ms"]
     return r
 
 
@@ -565,7 +583,9 @@ def p9_rows(dev):
     rows = {}
     for inst, precs in ((w.curve8192(p=9), ("fp32", "fp64")), (w.sphere128(p=9), ("fp32",))):
         f = torch.as_tensor(inst.sources()[0], device=dev)
-        ref_plan = Plan(inst.x, inst.k, inst.N, inst.p, precision="fp64")
+        # the FP64 direct sum does not depend on p: in 3D it comes from a p = 5 FP64 plan of
+        # the same points (3D p = 9 has no FP64 kernel)
+        ref_plan = Plan(inst.x, inst.k, inst.N, inst.p if "fp64" in precs else 5, precision="fp64")
         exact = ref_plan.direct(f)
         torch.cuda.synchronize()
         row = {"N": int(inst.N), "p": 9, "dim": inst.dim, "nx": int(inst.x.shape[0]), "nk": int(inst.k.shape[0])}
@@ -598,14 +618,20 @@ def main_batch(args):
     from paper_0801_1524_gb300.plan import Plan
     insts = w.star_batch(nrhs=args.nrhs)
     dev = torch.device("cuda", 0)
-    smem_kb = 0
+    smem_kb, stages, tuned = 0, 0, None
+    precs = tuple(args.precision.split(","))
     if args.autotune:  # one configuration for the whole batch, tuned on its largest instance
         big = max(insts, key=lambda I: I.N)
-        smem_kb = Plan(big.x, big.k, big.N, big.p, max_nrhs=args.nrhs, autotune=True).info()["smem_kb"]
+        t0 = time.perf_counter()
+        info = Plan(big.x, big.k, big.N, big.p, max_nrhs=args.nrhs, autotune=True).info()
+        names = {0: "fp64", 1: "fp32", 2: "tc"}
+        smem_kb, stages, precs = info["smem_kb"], info["stages_per_launch"], (names[info["prec"]],)
+        tuned = {"smem_kb": smem_kb, "stages_per_launch": stages, "precision": precs[0],
+                 "tuned_on": f"largest instance (N = {big.N:.0f})", "tuning_s": time.perf_counter() - t0}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     r = run_batch(insts, args.nrhs, args.steps, max(3, min(args.steps, 10)), args.warmup, dev, flush,
-                  smem_kb=smem_kb)
-    ms = r["ms"]
+                  smem_kb=smem_kb, precisions=precs, stages=stages)
+    ms = r[precs[0]]["ms"]
     pairs = sum(I.x.shape[0] * I.k.shape[0] for I in insts) * args.nrhs
     line = {"metric": METRIC + " (batched)", "value": len(insts) * args.nrhs * 1e3 / ms,
             "unit": "instance-RHS transforms/s", "ms_per_step": ms, "steps": args.steps,
@@ -615,8 +641,8 @@ def main_batch(args):
                        "sum_N": float(sum(I.N for I in insts)),
                        "l2": "flushed between steps (256 MB written, then read back)",
                        "points": int(sum(I.x.shape[0] + I.k.shape[0] for I in insts))},
-            "effective_IJ_per_s": pairs * 1e3 / ms, "smem_kb": smem_kb or None}
-    line.update({k: v for k, v in r.items() if k != "ms"})
+            "effective_IJ_per_s": pairs * 1e3 / ms, "autotuned": tuned}
+    line.update(r)
     return line
 
 

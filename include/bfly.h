@@ -43,8 +43,12 @@ typedef enum { BFLY_C64 = 0, BFLY_C128 = 1 } bfly_dtype;
 
 /* Arithmetic of the butterfly applies.  FP32: complex64 charges, FP32 operators and
  * accumulation, operators and per-point weights built in FP64.  FP64: complex128
- * throughout (the plain FP64 GPU butterfly). */
-typedef enum { BFLY_PREC_FP64 = 0, BFLY_PREC_FP32 = 1 } bfly_precision;
+ * throughout (the plain FP64 GPU butterfly).  TC (2D): the FP32 plan with the recursive
+ * step (Sec. 2.2 step 3) on the tensor cores for many right-hand sides: eight right-hand
+ * sides of a box pair form the columns of one real product R(C) X with the operator in
+ * real form, as TF32 MMAs compensated to FP32 accuracy (both operands split hi + lo,
+ * three products), FP32 accumulation; leaf and final steps as FP32. */
+typedef enum { BFLY_PREC_FP64 = 0, BFLY_PREC_FP32 = 1, BFLY_PREC_TC = 2 } bfly_precision;
 
 /* Build only the host plan: no device memory is touched, execution entry points return
  * BFLY_ERR_INVALID_ARG; bfly_plan_info and bfly_plan_stage still work.  */
@@ -54,11 +58,15 @@ typedef enum { BFLY_PREC_FP64 = 0, BFLY_PREC_FP32 = 1 } bfly_precision;
  * waits time out and set the device status word (results are then invalid). */
 #define BFLY_FLAG_TEST_STALL 2u
 
-/* Autotune the recursive step: build the plan for each candidate shared-memory budget
- * per block (which sets how much work one block takes at a time and how many blocks
- * share an SM), time a forward sweep of each with max_nrhs right-hand sides, and keep
- * the fastest.  With tune_cache set, a choice recorded there for the same GPU, dim, p,
- * precision, nrhs and size class is reused, and new choices are appended. */
+/* Autotune the recursive step: build the plan for each candidate configuration, time a
+ * forward sweep of each with max_nrhs right-hand sides (median of three after a warm-up),
+ * and keep the fastest.  Candidates: the shared-memory budget per block (which sets how
+ * many tiles, and so box pairs, one block takes at a time and how many blocks share an
+ * SM) x, in 2D, the stages per launch (3, 2, 1); and, for an FP32 plan in 2D with
+ * max_nrhs >= 8, the tensor-core recursive step (BFLY_PREC_TC) at two budgets and two
+ * stage counts.  With tune_cache set, a choice recorded there for the same GPU, dim, p,
+ * requested precision, nrhs and size class is reused, and new choices are appended.
+ * bfly_plan_info_t reports the chosen precision, budget and stages. */
 #define BFLY_FLAG_AUTOTUNE 4u
 /* One stage per launch of the recursive step also in 2D (no stages fused in shared
  * memory): the unfused programs of Sec. 2.2 step 3, for comparison and testing. */
@@ -69,9 +77,11 @@ typedef struct {
   int max_nrhs;            /* workspace is sized for up to this many right-hand sides (>= 1) */
   unsigned flags;          /* BFLY_FLAG_* */
   int smem_kb;             /* shared memory per block for the recursive step, 0 = default
-                              (55 KB in 2D, 73 KB in 3D) */
+                              (55 KB in 2D, 73 KB in 3D; 110 KB for BFLY_PREC_TC) */
   const char *tune_cache;  /* autotuning cache file (text), or NULL */
-  int reserved[2];         /* must be zero */
+  int stages;              /* 2D: at most this many stages per launch of the recursive step
+                              (1..3; 0 = default 3); BFLY_FLAG_ONE_STAGE sets 1 */
+  int reserved;            /* must be zero */
 } bfly_opts;
 
 typedef struct {
@@ -96,6 +106,7 @@ typedef struct {
   double plan_seconds;          /* host wall time of bfly_plan_create */
   int steps;                    /* launches of the recursive step per transform: up to three
                                    stages each in 2D, one in 3D (bfly_plan_step) */
+  int stages_per_launch;        /* the most stages of one launch the plan was built for */
 } bfly_plan_info_t;
 
 /*
@@ -116,7 +127,8 @@ typedef struct {
  *            its count is 0: the transform then returns zeros, or nothing).
  *   opts     NULL for defaults.
  * Errors: INVALID_ARG (any of the above), UNSUPPORTED (even p; N beyond 2^30 in 2D or
- * 2^20 in 3D; a p or precision whose workspace does not fit on chip), OUT_OF_MEMORY,
+ * 2^20 in 3D; BFLY_PREC_TC in 3D; a p or precision whose workspace does not fit on
+ * chip), OUT_OF_MEMORY,
  * CUDA.
  * The device current at the call owns the plan's memory; execute on that device.
  */

@@ -135,11 +135,13 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   o.prec = BFLY_PREC_FP32;
   o.max_nrhs = 1;
   if (opts) o = *opts;
-  if (o.prec != BFLY_PREC_FP32 && o.prec != BFLY_PREC_FP64)
+  if (o.prec != BFLY_PREC_FP32 && o.prec != BFLY_PREC_FP64 && o.prec != BFLY_PREC_TC)
     return fail(BFLY_ERR_INVALID_ARG, "unknown precision");
+  if (o.prec == BFLY_PREC_TC && dim != 2)
+    return fail(BFLY_ERR_UNSUPPORTED, "the tensor-core recursive step is built for dim = 2");
   if (o.max_nrhs < 1 || o.max_nrhs > 4096) return fail(BFLY_ERR_INVALID_ARG, "max_nrhs must be in 1..4096");
-  for (int i = 0; i < 2; ++i)
-    if (o.reserved[i] != 0) return fail(BFLY_ERR_INVALID_ARG, "reserved options must be zero");
+  if (o.reserved != 0) return fail(BFLY_ERR_INVALID_ARG, "reserved options must be zero");
+  if (o.stages < 0 || o.stages > bfly::kMaxLevels) return fail(BFLY_ERR_INVALID_ARG, "stages must be in 0..3");
   if ((o.flags & BFLY_FLAG_AUTOTUNE) && !(o.flags & BFLY_FLAG_HOST_ONLY))
     return autotune_create(out, dim, N, nx, x, nk, k, p, o);
 
@@ -193,7 +195,7 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
 
   const bool host_only = (o.flags & BFLY_FLAG_HOST_ONLY) != 0;
   // shared memory plan of the recursive step
-  P->ks = select_kernels(p, o.prec == BFLY_PREC_FP64 ? 0 : 1, dim);
+  P->ks = select_kernels(p, o.prec == BFLY_PREC_FP64 ? 0 : o.prec == BFLY_PREC_TC ? 2 : 1, dim);
   if (!P->ks) {
     delete P;
     return fail(BFLY_ERR_UNSUPPORTED, "no kernels for this (dim, p)");
@@ -214,9 +216,14 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   // capacities: the largest chunk that fits the shared-memory budget of one block
   // default budget: four blocks per SM in 2D; in 3D (8x larger tiles at p = 5) fewer,
   // larger blocks, whose chunks hold enough tiles to keep the consumer warps busy
-  const size_t want = (size_t)(o.smem_kb > 0 ? o.smem_kb : (dim == 3 ? 73 : 55)) * 1024;
+  // (tensor-core step: eight right-hand sides per tile slot, two blocks per SM)
+  const size_t want =
+      (size_t)(o.smem_kb > 0 ? o.smem_kb : o.prec == BFLY_PREC_TC ? 110 : (dim == 3 ? 73 : 55)) * 1024;
   auto caps_for = [&](size_t budget) {
-    for (int cap = 1024; cap >= 8; cap -= 8) {
+    // tile slots in steps of 8 (FP32, FP64); of 1 for the tensor-core step, whose slots hold
+    // eight right-hand sides each
+    const int step = o.prec == BFLY_PREC_TC ? 1 : 8;
+    for (int cap = 1024; cap >= step; cap -= step) {
       const ChunkCaps c{cap, cap, cap, P->ks->meta_bytes(cap, cap, cap)};
       if (P->ks->level_smem(c) <= budget) return c;
     }
@@ -258,12 +265,14 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     return bfly::StageTrees{&P->TX.cs[L - t - 1], &P->TX.idx[L - t], &P->TK.cs[t], &P->TK.idx[t + 1]};
   };
   std::deque<int> todo;
-  if (dim == 3 || (o.flags & BFLY_FLAG_ONE_STAGE)) {
+  const int max_lev = (dim == 3 || (o.flags & BFLY_FLAG_ONE_STAGE)) ? 1 : o.stages > 0 ? o.stages : bfly::kMaxLevels;
+  if (max_lev == 1) {
     todo.assign(L, 1);
   } else {
-    if (L % bfly::kMaxLevels) todo.push_back(L % bfly::kMaxLevels);
-    for (int i = 0; i < L / bfly::kMaxLevels; ++i) todo.push_back(bfly::kMaxLevels);
+    if (L % max_lev) todo.push_back(L % max_lev);
+    for (int i = 0; i < L / max_lev; ++i) todo.push_back(max_lev);
   }
+  I.stages_per_launch = max_lev;
   // the programs of the planned steps, forward and adjoint, compiled on all host cores
   // (each is independent); a step split after a capacity failure is compiled below
   struct Compiled {
@@ -691,27 +700,39 @@ std::string tune_key(int dim, int p, int prec, int nrhs, int64_t max_pairs) {
          " nrhs" + std::to_string(nrhs) + " pairs2^" + std::to_string(size_class);
 }
 
-int cache_lookup(const char *path, const std::string &key) {
-  if (!path) return 0;
+// One configuration of the recursive step: shared-memory budget per block, stages per
+// launch (2D), precision of the applies.
+struct TuneChoice {
+  int smem_kb = 0, stages = 0, prec = -1;
+};
+
+// The last choice recorded for `key` ("<key> <smem_kb> [<stages> <prec>]" lines), or
+// smem_kb = 0 when there is none.
+TuneChoice cache_lookup(const char *path, const std::string &key) {
+  TuneChoice found;
+  if (!path) return found;
   FILE *fh = std::fopen(path, "r");
-  if (!fh) return 0;
+  if (!fh) return found;
   char line[512];
-  int found = 0;
   while (std::fgets(line, sizeof line, fh)) {
     std::string l(line);
-    const size_t sp = l.rfind(' ');
-    if (sp == std::string::npos) continue;
-    if (l.compare(0, sp, key) == 0) found = std::atoi(l.c_str() + sp + 1);
+    if (l.compare(0, key.size(), key) != 0 || l.size() <= key.size() || l[key.size()] != ' ') continue;
+    TuneChoice c;
+    const int n = std::sscanf(l.c_str() + key.size(), " %d %d %d", &c.smem_kb, &c.stages, &c.prec);
+    if (n >= 1 && c.smem_kb > 0) {
+      if (n < 3) c.stages = 0, c.prec = -1;
+      found = c;
+    }
   }
   std::fclose(fh);
   return found;
 }
 
-void cache_store(const char *path, const std::string &key, int smem_kb) {
+void cache_store(const char *path, const std::string &key, const TuneChoice &c) {
   if (!path) return;
   FILE *fh = std::fopen(path, "a");
   if (!fh) return;
-  std::fprintf(fh, "%s %d\n", key.c_str(), smem_kb);
+  std::fprintf(fh, "%s %d %d %d\n", key.c_str(), c.smem_kb, c.stages, c.prec);
   std::fclose(fh);
 }
 
@@ -753,20 +774,42 @@ bfly_status autotune_create(bfly_plan_t *out, int dim, double N, int64_t nx, con
   if (st != BFLY_OK) return st;
   const std::string key = tune_key(dim, p, o.prec, o.max_nrhs, H->info.max_pairs);
   bfly_plan_destroy(H);
-  const int cached = cache_lookup(o.tune_cache, key);
-  if (cached > 0) {
-    o.smem_kb = cached;
-    return bfly_plan_create(out, dim, N, nx, x, nk, k, p, &o);
+  auto with = [&](const TuneChoice &c) {
+    bfly_opts r = o;
+    r.smem_kb = c.smem_kb;
+    if (c.stages > 0) r.stages = c.stages;
+    if (c.prec >= 0) r.prec = c.prec;
+    return r;
+  };
+  const TuneChoice cached = cache_lookup(o.tune_cache, key);
+  if (cached.smem_kb > 0) {
+    const bfly_opts r = with(cached);
+    return bfly_plan_create(out, dim, N, nx, x, nk, k, p, &r);
   }
-  const int candidates[] = {40, 55, 73, 110, 220};
+  // candidates: budgets x stages per launch (2D); the tensor-core step for FP32 plans in
+  // 2D with at least eight right-hand sides
+  std::vector<TuneChoice> cands;
+  const bool fixed_stages = o.stages > 0 || (o.flags & BFLY_FLAG_ONE_STAGE);
+  if (dim == 2) {
+    for (int stg : {3, 2, 1}) {
+      if (fixed_stages && stg != (o.stages > 0 ? o.stages : 1)) continue;
+      for (int kb : {40, 55, 73, 110}) cands.push_back({kb, stg, o.prec});
+    }
+    if (o.prec == BFLY_PREC_FP32 && o.max_nrhs >= 8)
+      for (int stg : {3, 1}) {
+        if (fixed_stages && stg != (o.stages > 0 ? o.stages : 1)) continue;
+        for (int kb : {110, 220}) cands.push_back({kb, stg, BFLY_PREC_TC});
+      }
+  } else {
+    for (int kb : {40, 55, 73, 110, 220}) cands.push_back({kb, 0, o.prec});
+  }
   bfly_plan_t best = nullptr;
   double best_ms = 0;
-  int best_kb = 0;
-  for (int kb : candidates) {
-    bfly_opts c = o;
-    c.smem_kb = kb;
+  TuneChoice best_c;
+  for (const TuneChoice &c : cands) {
+    const bfly_opts r = with(c);
     bfly_plan_t P = nullptr;
-    if (bfly_plan_create(&P, dim, N, nx, x, nk, k, p, &c) != BFLY_OK) continue;
+    if (bfly_plan_create(&P, dim, N, nx, x, nk, k, p, &r) != BFLY_OK) continue;
     double ms = 0;
     if (time_plan(P, &ms) != BFLY_OK) {
       bfly_plan_destroy(P);
@@ -776,14 +819,14 @@ bfly_status autotune_create(bfly_plan_t *out, int dim, double N, int64_t nx, con
       if (best) bfly_plan_destroy(best);
       best = P;
       best_ms = ms;
-      best_kb = kb;
+      best_c = c;
     } else {
       bfly_plan_destroy(P);
     }
   }
   if (!best) return fail(BFLY_ERR_UNSUPPORTED, "autotuning: no candidate configuration could be built");
   best->info.tuned_ms = best_ms;
-  cache_store(o.tune_cache, key, best_kb);
+  cache_store(o.tune_cache, key, best_c);
   g_err.clear();
   *out = best;
   return BFLY_OK;

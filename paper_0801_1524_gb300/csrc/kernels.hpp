@@ -23,7 +23,8 @@ struct KernelSet {
 };
 
 
-// prec: 0 = FP64, 1 = FP32.  Returns nullptr when (dim, p) has no kernels.
+// prec: 0 = FP64, 1 = FP32, 2 = FP32 with the recursive step on the tensor cores (2D).
+// Returns nullptr when (prec, dim, p) has no kernels.
 const KernelSet *kernels_p3(int prec, int dim);
 const KernelSet *kernels_p5(int prec, int dim);
 const KernelSet *kernels_p7(int prec, int dim);

@@ -11,7 +11,7 @@ BFLY_OK = 0
 BFLY_ERR_INVALID_ARG = 1
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "UNSUPPORTED", 5: "TIMEOUT"}
 BFLY_C64, BFLY_C128 = 0, 1
-BFLY_PREC_FP64, BFLY_PREC_FP32 = 0, 1
+BFLY_PREC_FP64, BFLY_PREC_FP32, BFLY_PREC_TC = 0, 1, 2
 BFLY_FLAG_HOST_ONLY = 1
 BFLY_FLAG_TEST_STALL = 2
 BFLY_FLAG_AUTOTUNE = 4
@@ -24,7 +24,7 @@ _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_doub
 class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("max_nrhs", ctypes.c_int), ("flags", ctypes.c_uint),
                 ("smem_kb", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
-                ("reserved", ctypes.c_int * 2)]
+                ("stages", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -38,7 +38,8 @@ class PlanInfo(ctypes.Structure):
                 ("flops_fwd", ctypes.c_double), ("lane_use_fwd", ctypes.c_double),
                 ("smem_kb", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("tuned_ms", ctypes.c_double),
-                ("plan_seconds", ctypes.c_double), ("steps", ctypes.c_int)]
+                ("plan_seconds", ctypes.c_double), ("steps", ctypes.c_int),
+                ("stages_per_launch", ctypes.c_int)]
 
 
 SIGNATURES = {

@@ -9,7 +9,7 @@ import numpy as np
 
 from . import native
 
-PRECISIONS = {"fp64": native.BFLY_PREC_FP64, "fp32": native.BFLY_PREC_FP32}
+PRECISIONS = {"fp64": native.BFLY_PREC_FP64, "fp32": native.BFLY_PREC_FP32, "tc": native.BFLY_PREC_TC}
 
 
 def _torch():
@@ -42,7 +42,7 @@ class Plan:
 
     def __init__(self, x, k, N: float, p: int, precision: str = "fp32", max_nrhs: int = 1,
                  host_only: bool = False, smem_kb: int = 0, flags: int = 0,
-                 autotune: bool = False, tune_cache: str | None = None):
+                 autotune: bool = False, tune_cache: str | None = None, stages: int = 0):
         lib = native.load()
         x = np.ascontiguousarray(x, dtype=np.float64)
         k = np.ascontiguousarray(k, dtype=np.float64)
@@ -54,7 +54,7 @@ class Plan:
         self.N = float(N)
         self.p = int(p)
         self.nx, self.nk = x.shape[0], k.shape[0]
-        self.precision = precision
+        self.precision = precision  # requested; info()["prec"] is the one built (autotuning)
         self.max_nrhs = int(max_nrhs)
         opts = native.Opts()
         opts.prec = PRECISIONS[precision]
@@ -62,6 +62,7 @@ class Plan:
         opts.flags = ((native.BFLY_FLAG_HOST_ONLY if host_only else 0) |
                       (native.BFLY_FLAG_AUTOTUNE if autotune else 0) | int(flags))
         opts.smem_kb = int(smem_kb)
+        opts.stages = int(stages)
         self._tune_cache = tune_cache.encode() if tune_cache else None
         opts.tune_cache = self._tune_cache
         h = ctypes.c_void_p()
