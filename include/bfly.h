@@ -196,6 +196,31 @@ bfly_status bfly_execute_events(bfly_plan_t plan, const void *in, void *out, int
                                 int n_events);
 
 /*
+ * Split sweep, for a transform sharded over ranks (the paper has no counterpart; the
+ * sweep is Sec. 2.2 steps 2-4 cut at stage t): the first part runs the leaf step and the
+ * recursive step down to stage t, the second from stage t on down to stage 0 and the final
+ * step.  Ranks that own subtrees of T_K run the first part on their sources, exchange the
+ * stage-t charges, and ranks that own subtrees of T_X run the second part for their
+ * targets (paper_0801_1524_gb300/sharded.py).
+ *   charges  device [nrhs][nA(L-t) * nB(t)][TS] equivalent charges of stage t in the plan's
+ *            precision (complex64 or complex128 interleaved), tile iA * nB + iB in the order
+ *            of bfly_plan_boxes, TS = the plan's tile stride (p^dim rounded up to an even
+ *            count in FP32, p^dim in FP64), rescaled as the recursive step keeps them
+ *            (g^{AB}_m = prod_d e^{2 pi i a_d m_d / (p-1)} f^{AB}_m, a the index of A).
+ *   t        a stage at a launch boundary of the plan: L, or the last stage of one of the
+ *            launches of bfly_plan_step (plans built with stages = 1 have every stage);
+ *            otherwise BFLY_ERR_INVALID_ARG.
+ * bfly_execute_to_stage   f device [nrhs][nk] (dtype) -> charges of stage t.
+ * bfly_execute_from_stage charges of stage t -> u device [nrhs][nx] (dtype).
+ * bfly_execute_to_stage(t = 0) followed by bfly_execute_from_stage(t = 0) is bfly_execute.
+ * Asynchronous on `stream`; they copy the stage through the plan's charge buffers.
+ */
+bfly_status bfly_execute_to_stage(bfly_plan_t plan, const void *f, int t, void *charges, int nrhs, int dtype,
+                                  void *stream);
+bfly_status bfly_execute_from_stage(bfly_plan_t plan, const void *charges, int t, void *u, int nrhs, int dtype,
+                                    void *stream);
+
+/*
  * bfly_execute_noalloc — bfly_execute (forward, device buffers) without any allocation:
  * the two charge buffers of the sweep come from a static device array owned by the
  * library (64 MiB in all, 32 MiB per buffer) instead of the plan's workspace.  The paper

@@ -591,6 +591,93 @@ bfly_status bfly_execute_events(bfly_plan_t plan, const void *in, void *out, int
              reinterpret_cast<cudaEvent_t const *>(events));
 }
 
+}  // extern "C"
+
+namespace {
+
+// The boundary b of the plan's launches (0: stage L; s + 1: after recursive-step launch s)
+// holding stage t, or -1 when no launch ends at stage t.
+int boundary_of(bfly_plan_t P, int t) {
+  if (t == P->L) return 0;
+  for (size_t s = 0; s < P->steps.size(); ++s)
+    if (P->steps[s].t - P->steps[s].levels + 1 == t) return (int)s + 1;
+  return -1;
+}
+
+// Arguments of the split sweep: a device plan, the point-side pointer (NULL only when
+// that side has no points), nrhs and dtype.
+bfly_status check_split(bfly_plan_t P, const void *v, int64_t n, int nrhs, int dtype) {
+  if (!P) return fail(BFLY_ERR_INVALID_ARG, "plan is NULL");
+  if (!P->dmem) return fail(BFLY_ERR_INVALID_ARG, "plan was created host-only");
+  if (!v && n > 0) return fail(BFLY_ERR_INVALID_ARG, "data pointer is NULL");
+  if (nrhs < 1 || nrhs > P->max_nrhs) return fail(BFLY_ERR_INVALID_ARG, "nrhs outside 1..max_nrhs");
+  if (dtype != BFLY_C64 && dtype != BFLY_C128) return fail(BFLY_ERR_INVALID_ARG, "unknown dtype");
+  return BFLY_OK;
+}
+
+bfly_status check_stage(bfly_plan_t P, int t, const void *charges, int *b) {
+  if (t < 0 || t > P->L) return fail(BFLY_ERR_INVALID_ARG, "stage outside 0..L");
+  *b = boundary_of(P, t);
+  if (*b < 0)
+    return fail(BFLY_ERR_INVALID_ARG, "stage " + std::to_string(t) +
+                                          " is not at a launch boundary of the plan (bfly_plan_step; "
+                                          "stages = 1 makes every stage one)");
+  if (!charges && P->pairs[t] > 0) return fail(BFLY_ERR_INVALID_ARG, "charges pointer is NULL");
+  return BFLY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bfly_status bfly_execute_to_stage(bfly_plan_t plan, const void *f, int t, void *charges, int nrhs, int dtype,
+                                  void *stream) {
+  g_err.clear();
+  bfly_status st = check_split(plan, f, plan ? plan->nk : 0, nrhs, dtype);
+  if (st != BFLY_OK) return st;
+  int b = 0;
+  st = check_stage(plan, t, charges, &b);
+  if (st != BFLY_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool io64 = dtype == BFLY_C128;
+  const size_t bytes = (size_t)nrhs * plan->pairs[t] * plan->TS * plan->elem_bytes;
+  if (plan->nk == 0 || plan->nx == 0) {  // no sources: zero charges; no targets: no tiles
+    if (bytes) BFLY_CUDA(cudaMemsetAsync(charges, 0, bytes, s));
+    return BFLY_OK;
+  }
+  BFLY_CUDA(plan->ks->spread(point_args(plan, false, f, plan->buf[0], nrhs, io64, false,
+                                        plan->pairs[plan->L] * plan->TS), s));
+  for (int si = 0; si < b; ++si)
+    BFLY_CUDA(plan->ks->level(level_args(plan, si, false, nrhs), false, plan->level_grid, plan->level_smem, s));
+  if (bytes) BFLY_CUDA(cudaMemcpyAsync(charges, plan->buf[b & 1], bytes, cudaMemcpyDeviceToDevice, s));
+  return BFLY_OK;
+}
+
+bfly_status bfly_execute_from_stage(bfly_plan_t plan, const void *charges, int t, void *u, int nrhs, int dtype,
+                                    void *stream) {
+  g_err.clear();
+  bfly_status st = check_split(plan, u, plan ? plan->nx : 0, nrhs, dtype);
+  if (st != BFLY_OK) return st;
+  int b = 0;
+  st = check_stage(plan, t, charges, &b);
+  if (st != BFLY_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool io64 = dtype == BFLY_C128;
+  if (plan->nx == 0) return BFLY_OK;
+  if (plan->nk == 0) {
+    BFLY_CUDA(cudaMemsetAsync(u, 0, (size_t)nrhs * plan->nx * (io64 ? 16 : 8), s));
+    return BFLY_OK;
+  }
+  const size_t bytes = (size_t)nrhs * plan->pairs[t] * plan->TS * plan->elem_bytes;
+  const int S = (int)plan->steps.size();
+  if (bytes) BFLY_CUDA(cudaMemcpyAsync(plan->buf[b & 1], charges, bytes, cudaMemcpyDeviceToDevice, s));
+  for (int si = b; si < S; ++si)
+    BFLY_CUDA(plan->ks->level(level_args(plan, si, false, nrhs), false, plan->level_grid, plan->level_smem, s));
+  BFLY_CUDA(plan->ks->interp(point_args(plan, true, plan->buf[S & 1], u, nrhs, io64, false,
+                                        plan->pairs[0] * plan->TS), s));
+  return BFLY_OK;
+}
+
 bfly_status bfly_direct(bfly_plan_t plan, const void *in, void *out, int nrhs, int dtype, int adjoint,
                         void *stream) {
   g_err.clear();

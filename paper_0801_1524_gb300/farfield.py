@@ -74,10 +74,3 @@ class FarField:
         g = torch.as_tensor(self.strengths(f)).to(device="cuda", dtype=dt)
         return self.plan.forward(g)
 
-
-def sphere_far_field_exact(xh, N: float, radius: float = 0.4, centre=(0.5, 0.5, 0.5)):
-    """u_inf of the density f = 1 on the sphere |y - centre| = radius:
-    4 pi R^2 j0(N R) exp(-i N xh . centre), j0(z) = sin z / z."""
-    z = float(N) * radius
-    c = np.asarray(centre, dtype=np.float64)
-    return 4.0 * np.pi * radius ** 2 * (np.sin(z) / z) * np.exp(-1j * float(N) * (np.asarray(xh) @ c))

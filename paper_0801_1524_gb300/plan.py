@@ -195,6 +195,48 @@ class Plan:
         return self._run(self._lib.bfly_execute_noalloc, f, self.nk, self.nx, out, stream,
                          "bfly_execute_noalloc")
 
+    def _charge_dtype(self):
+        torch = _torch()
+        return torch.complex128 if self.precision == "fp64" or self.info()["prec"] == native.BFLY_PREC_FP64 \
+            else torch.complex64
+
+    def boundaries(self) -> list:
+        """Stages at the launch boundaries of the sweep (where it can be split): L and the
+        last stage of every recursive-step launch."""
+        return [self.info()["L"]] + [t - lev + 1 for t, lev in self.steps()]
+
+    def to_stage(self, f, t: int, out=None, stream=None):
+        """bfly_execute_to_stage: the leaf step and the recursive step down to stage t;
+        returns the stage-t charges [nrhs, nA * nB * TS] (plan precision, plan tile order)."""
+        torch = _torch()
+        s, _ = self._prep(f, self.nk, "f")
+        nA, nB = self.stages()[t][1:]
+        pd = self.p ** self.dim
+        ts = pd if self._charge_dtype() == torch.complex128 else pd + (pd & 1)
+        if out is None:
+            out = torch.empty((s.shape[0], nA * nB * ts), dtype=self._charge_dtype(), device=s.device)
+        if out.dtype != self._charge_dtype() or not out.is_contiguous() or out.numel() != s.shape[0] * nA * nB * ts:
+            raise ValueError("charges must be contiguous [nrhs, nA * nB * TS] of the plan's precision")
+        native.check(self._lib.bfly_execute_to_stage(self._h, ctypes.c_void_p(s.data_ptr()), int(t),
+                                                     ctypes.c_void_p(out.data_ptr()), s.shape[0],
+                                                     _dtype_code(s), _stream_ptr(stream)), "bfly_execute_to_stage")
+        return out
+
+    def from_stage(self, charges, t: int, out=None, dtype=None, stream=None):
+        """bfly_execute_from_stage: stage-t charges -> potentials [nrhs, nx] (dtype: the
+        charges' complex type unless given)."""
+        torch = _torch()
+        c = charges.contiguous()
+        if c.dtype != self._charge_dtype():
+            raise ValueError("charges must have the plan's precision")
+        nrhs = c.shape[0]
+        if out is None:
+            out = torch.empty((nrhs, self.nx), dtype=dtype or c.dtype, device=c.device)
+        native.check(self._lib.bfly_execute_from_stage(self._h, ctypes.c_void_p(c.data_ptr()), int(t),
+                                                       ctypes.c_void_p(out.data_ptr()), nrhs, _dtype_code(out),
+                                                       _stream_ptr(stream)), "bfly_execute_from_stage")
+        return out
+
     def adjoint(self, u, out=None, stream=None):
         return self._run(self._lib.bfly_execute_adjoint, u, self.nx, self.nk, out, stream,
                          "bfly_execute_adjoint")
