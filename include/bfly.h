@@ -62,7 +62,7 @@ typedef enum { BFLY_PREC_FP64 = 0, BFLY_PREC_FP32 = 1, BFLY_PREC_TC = 2 } bfly_p
  * forward sweep of each with max_nrhs right-hand sides (median of three after a warm-up),
  * and keep the fastest.  Candidates: the shared-memory budget per block (which sets how
  * many tiles, and so box pairs, one block takes at a time and how many blocks share an
- * SM) x, in 2D, the stages per launch (3, 2, 1); and, for an FP32 plan in 2D with
+ * SM) x the stages per launch (2D: 3, 2, 1; 3D: 1, 2); and, for an FP32 plan in 2D with
  * max_nrhs >= 8, the tensor-core recursive step (BFLY_PREC_TC) at two budgets and two
  * stage counts.  With tune_cache set, a choice recorded there for the same GPU, dim, p,
  * requested precision, nrhs and size class is reused, and new choices are appended.
@@ -79,8 +79,9 @@ typedef struct {
   int smem_kb;             /* shared memory per block for the recursive step, 0 = default
                               (55 KB in 2D, 73 KB in 3D; 110 KB for BFLY_PREC_TC) */
   const char *tune_cache;  /* autotuning cache file (text), or NULL */
-  int stages;              /* 2D: at most this many stages per launch of the recursive step
-                              (1..3; 0 = default 3); BFLY_FLAG_ONE_STAGE sets 1 */
+  int stages;              /* at most this many stages per launch of the recursive step:
+                              2D 1..3 (0 = default 3), 3D 1..2 (0 = default 1; larger
+                              values are taken as 2); BFLY_FLAG_ONE_STAGE sets 1 */
   int reserved;            /* must be zero */
 } bfly_opts;
 

@@ -265,7 +265,12 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     return bfly::StageTrees{&P->TX.cs[L - t - 1], &P->TX.idx[L - t], &P->TK.cs[t], &P->TK.idx[t + 1]};
   };
   std::deque<int> todo;
-  const int max_lev = (dim == 3 || (o.flags & BFLY_FLAG_ONE_STAGE)) ? 1 : o.stages > 0 ? o.stages : bfly::kMaxLevels;
+  // stages per launch: 2D up to three (default three); 3D up to two (default one: a 3D
+  // two-level unit holds up to 64 input tiles of p^3 values, which only the sparse boxes
+  // of surfaces keep within a block's shared memory)
+  const int max_lev = (o.flags & BFLY_FLAG_ONE_STAGE) ? 1
+                      : dim == 3 ? std::min(o.stages > 0 ? o.stages : 1, bfly::kMaxPasses / 3)
+                                 : (o.stages > 0 ? o.stages : bfly::kMaxLevels);
   if (max_lev == 1) {
     todo.assign(L, 1);
   } else {
@@ -888,6 +893,8 @@ bfly_status autotune_create(bfly_plan_t *out, int dim, double N, int64_t nx, con
         for (int kb : {110, 220}) cands.push_back({kb, stg, BFLY_PREC_TC});
       }
   } else {
+    // 3D: one stage per launch unless asked (the units of two stages of surfaces exceed a
+    // block's shared memory, and the plan then falls back to one stage anyway)
     for (int kb : {40, 55, 73, 110, 220}) cands.push_back({kb, 0, o.prec});
   }
   bfly_plan_t best = nullptr;

@@ -27,7 +27,7 @@ constexpr int kSpreadPerThread = 4;  // tile elements per thread
 // from memory once and the loads of a batch are in flight together; then each thread sums
 // the batch's points of its elements' leaves.
 template <typename R, int D, int P>
-__global__ void __launch_bounds__(kPointThreads) spread_kernel(const PointArgs a) {
+__global__ void __launch_bounds__(kPointThreads, 4) spread_kernel(const PointArgs a) {
   using C = typename Cx<R>::T;
   constexpr int PD = ipow(P, D), E = kPointThreads * kSpreadPerThread;
   constexpr int BATCH = (24576 / ((D * P + 1) * (int)sizeof(C))) / 32 * 32;
@@ -36,56 +36,77 @@ __global__ void __launch_bounds__(kPointThreads) spread_kernel(const PointArgs a
   const int64_t n_el = a.nbox * PD;
   const int64_t e0 = (int64_t)blockIdx.x * E;
   const int r = blockIdx.y;
-  int64_t bk[kSpreadPerThread];
-  int lk[kSpreadPerThread][D], j0[kSpreadPerThread], j1[kSpreadPerThread];
+  // element k of this thread: tile element l (< PD) of leaf bk (the plan's leaves number
+  // fewer than 2^31), its points j0 .. j1 - 1 in sorted order
+  int bk[kSpreadPerThread], lt[kSpreadPerThread], j0[kSpreadPerThread], j1[kSpreadPerThread];
   C acc[kSpreadPerThread];
 #pragma unroll
   for (int k = 0; k < kSpreadPerThread; ++k) {
     const int64_t w = e0 + threadIdx.x + k * kPointThreads;
     const bool on = w < n_el;
-    bk[k] = on ? w / PD : -1;
-    int rem = on ? (int)(w - bk[k] * PD) : 0;
-#pragma unroll
-    for (int d = D - 1; d >= 0; --d) {
-      lk[k][d] = rem % P;
-      rem /= P;
-    }
+    bk[k] = on ? (int)(w / PD) : -1;
+    lt[k] = on ? (int)(w - (int64_t)bk[k] * PD) : 0;
     j0[k] = on ? a.leaf_start[bk[k]] : 0;
     j1[k] = on ? a.leaf_start[bk[k] + 1] : 0;
     acc[k] = cmk((R)0, (R)0);
   }
   pdl_trigger();
-  pdl_wait();  // the point values and the output tiles belong to the predecessor's stream
-  // the block's points: those of leaves e0/PD .. (last element)/PD
+  // the block's points: those of leaves e0/PD .. (last element)/PD.  The leaf ranges, the
+  // permutation and the weights are plan data, read before the dependency wait; only the
+  // point values (the caller's) and the output tiles (read by the predecessor's sweep)
+  // wait for the predecessor grid.
   const int64_t e1 = min(n_el, e0 + E);
   const int jb0 = a.leaf_start[e0 / PD], jb1 = a.leaf_start[(e1 - 1) / PD + 1];
   const C *W = reinterpret_cast<const C *>(a.W);
+  constexpr int PJ = (BATCH + kPointThreads - 1) / kPointThreads;
+  bool waited = false;
   for (int pb = jb0; pb < jb1; pb += BATCH) {
     const int n = min(BATCH, jb1 - pb);
-    for (int t = threadIdx.x; t < n; t += kPointThreads)
-      s_v[t] = load_io<C>(a.vin, (int64_t)r * a.n_total + a.perm[pb + t], a.io64);
+    int pj[PJ];
+#pragma unroll
+    for (int q = 0; q < PJ; ++q) {
+      const int t = threadIdx.x + q * kPointThreads;
+      pj[q] = t < n ? a.perm[pb + t] : 0;
+    }
     for (int t = threadIdx.x; t < n * D * P; t += kPointThreads) {
       const C wv = W[(size_t)pb * D * P + t];
       s_w[t / (D * P)][t % (D * P)] = a.conj ? cconj(wv) : wv;
+    }
+    if (!waited) {
+      pdl_wait();
+      waited = true;
+    }
+#pragma unroll
+    for (int q = 0; q < PJ; ++q) {
+      const int t = threadIdx.x + q * kPointThreads;
+      if (t < n) s_v[t] = load_io<C>(a.vin, (int64_t)r * a.n_total + pj[q], a.io64);
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kSpreadPerThread; ++k) {
       const int ja = max(j0[k], pb) - pb, jz = min(j1[k], pb + n) - pb;
-      for (int j = ja; j < jz; ++j) {
-        C wt = s_w[j][lk[k][0]];
+      // the index of element l along each axis (axis 0 slowest)
+      int ld[D];
+      int rem = lt[k];
 #pragma unroll
-        for (int d = 1; d < D; ++d) wt = cmul(wt, s_w[j][d * P + lk[k][d]]);
+      for (int d = D - 1; d >= 0; --d) {
+        ld[d] = rem % P;
+        rem /= P;
+      }
+      for (int j = ja; j < jz; ++j) {
+        C wt = s_w[j][ld[0]];
+#pragma unroll
+        for (int d = 1; d < D; ++d) wt = cmul(wt, s_w[j][d * P + ld[d]]);
         acc[k] = cfma(wt, s_v[j], acc[k]);
       }
     }
     __syncthreads();
   }
+  if (!waited) pdl_wait();
 #pragma unroll
   for (int k = 0; k < kSpreadPerThread; ++k)
     if (bk[k] >= 0) {
-      const int l = (int)(e0 + threadIdx.x + k * kPointThreads - bk[k] * PD);
-      reinterpret_cast<C *>(a.vout)[(size_t)r * a.tile_rhs + (size_t)bk[k] * a.tile_stride + l] = acc[k];
+      reinterpret_cast<C *>(a.vout)[(size_t)r * a.tile_rhs + (size_t)bk[k] * a.tile_stride + lt[k]] = acc[k];
     }
 }
 
