@@ -43,12 +43,14 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0,
                     help="target wall time of the oracle CPU baseline sample")
     ap.add_argument("--no-baselines", action="store_true")
-    ap.add_argument("--nrhs", type=int, default=16, help="right-hand sides (star_batch)")
+    ap.add_argument("--nrhs", type=int, default=None,
+                    help="right-hand sides (default: 1; star_batch: 16)")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--smem-kb", type=int, default=0,
                     help="shared memory per block of the recursive step (0 = the library default)")
     ap.add_argument("--precision", default="fp32",
-                    help="star_batch: comma-separated precisions of the batch (fp32, tc); the first is the value")
+                    help="precision of the timed path (fp32, tc); star_batch: comma-separated "
+                         "precisions of the batch, the first is the value")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and p = 9 companion measurements of the default run")
     return ap.parse_args()
@@ -85,12 +87,12 @@ def workload(name):
     return w.WORKLOADS[name]()
 
 
-def describe(inst):
+def describe(inst, nrhs=1):
     return {"workload": f"{inst.name}: {inst.dim}D, N={int(inst.N)}, p={inst.p}, "
-                        f"{inst.x.shape[0]} targets, {inst.k.shape[0]} sources, 1 RHS, "
+                        f"{inst.x.shape[0]} targets, {inst.k.shape[0]} sources, {nrhs} RHS, "
                         "complex64 Gaussian sources (seed 0)",
             "N": int(inst.N), "p": inst.p, "dim": inst.dim, "nx": int(inst.x.shape[0]),
-            "nk": int(inst.k.shape[0]), "nrhs": 1,
+            "nk": int(inst.k.shape[0]), "nrhs": nrhs,
             "l2": "flushed between steps (256 MB written, then read back so that no dirty line "
                   "is left for the timed kernels to write back); per-step CUDA events"}
 
@@ -202,14 +204,17 @@ def main_bfly(args, rank, world, dist):
     torch.cuda.set_device(dev)
     inst = workload(args.workload)
     nx, nk = inst.x.shape[0], inst.k.shape[0]
-    f_np = inst.sources(dtype=np.complex64)[0]
+    nrhs = args.nrhs or 1
+    prec = args.precision.split(",")[0]
+    shp = lambda n: (n,) if nrhs == 1 else (nrhs, n)
+    f_np = inst.sources(dtype=np.complex64, nrhs=nrhs).reshape(shp(nk))
     stream = torch.cuda.current_stream()
     f = torch.as_tensor(f_np, device=dev)
-    plan = Plan(inst.x, inst.k, inst.N, inst.p, precision="fp32", smem_kb=args.smem_kb)
+    plan = Plan(inst.x, inst.k, inst.N, inst.p, precision=prec, smem_kb=args.smem_kb, max_nrhs=nrhs)
     info = plan.info()
     L = info["L"]
     S = info["steps"]    # recursive-step launches per transform
-    u = torch.empty(nx, dtype=torch.complex64, device=dev)
+    u = torch.empty(shp(nx), dtype=torch.complex64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     alu = alu_peaks()
 
@@ -264,24 +269,24 @@ def main_bfly(args, rank, world, dist):
     clk = clocks.stop() if clocks else None
 
     # ---- end to end through the host-buffer C-ABI call (copies inside the timed call)
-    f_pin = torch.empty(nk, dtype=torch.complex64).pin_memory()
+    f_pin = torch.empty(shp(nk), dtype=torch.complex64).pin_memory()
     f_pin.copy_(torch.as_tensor(f_np))
-    u_pin = torch.empty(nx, dtype=torch.complex64).pin_memory()
+    u_pin = torch.empty(shp(nx), dtype=torch.complex64).pin_memory()
     f_host = f_pin.numpy()
     u_host = u_pin.numpy()
     for _ in range(3):
-        plan.execute_host(f_host, out=u_host.reshape(1, -1))
+        plan.execute_host(f_host, out=u_host.reshape(nrhs, -1))
     e2e = []
     for _ in range(max(10, min(args.steps, 100))):
         flush_l2(flush)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        plan.execute_host(f_host, out=u_host.reshape(1, -1))
+        plan.execute_host(f_host, out=u_host.reshape(nrhs, -1))
         e2e.append(time.perf_counter() - t0)
     e2e_s = float(np.mean(e2e))
 
     # ---- the adjoint sweep (the gradient's transform) on the same plan, device buffers
-    v_adj = torch.empty(nk, dtype=torch.complex64, device=dev)
+    v_adj = torch.empty(shp(nk), dtype=torch.complex64, device=dev)
     for _ in range(3):
         plan.adjoint(u, out=v_adj)
     adj_ms = []
@@ -301,9 +306,9 @@ def main_bfly(args, rank, world, dist):
     out = {}
     u32 = u.to(torch.complex128)
     if not args.no_baselines:
-        plan64 = Plan(inst.x, inst.k, inst.N, inst.p, precision="fp64")
+        plan64 = Plan(inst.x, inst.k, inst.N, inst.p, precision="fp64", max_nrhs=nrhs)
         f64 = f.to(torch.complex128)
-        u64 = torch.empty(nx, dtype=torch.complex128, device=dev)
+        u64 = torch.empty(shp(nx), dtype=torch.complex128, device=dev)
         for _ in range(3):
             plan64.forward(f64, out=u64)
         torch.cuda.synchronize()
@@ -319,14 +324,14 @@ def main_bfly(args, rank, world, dist):
         ms64 = float(np.mean([a.elapsed_time(b) for a, b in ev64]))
         rel_vs_fp64 = (torch.linalg.norm(u32 - u64) / torch.linalg.norm(u64)).item()
         # direct sums on the GPU (eq. 1.1), FP64 phase reduction
-        ud = torch.empty(nx, dtype=torch.complex128, device=dev)
+        ud = torch.empty(shp(nx), dtype=torch.complex128, device=dev)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         plan64.direct(f64, out=ud)
         b.record(stream)
         torch.cuda.synchronize()
         ms_direct64 = a.elapsed_time(b)
-        ud32 = torch.empty(nx, dtype=torch.complex64, device=dev)
+        ud32 = torch.empty(shp(nx), dtype=torch.complex64, device=dev)
         a.record(stream)
         plan.direct(f, out=ud32)
         b.record(stream)
@@ -353,11 +358,11 @@ def main_bfly(args, rank, world, dist):
     # 2p^3 complex multiply-adds in 2D (3p^4 in 3D), 8 real flops each; the tiles of the
     # stages between launches read once and written once (p^d complex64 each; the stage
     # inside a two-stage launch stays in shared memory)
-    flops = info["jobs_fwd"] * (2 * p ** 3 if d == 2 else 3 * p ** 4) * 8.0
-    flops_exec = info["flops_fwd"]     # as executed (sum factorisation shares work)
+    flops = info["jobs_fwd"] * (2 * p ** 3 if d == 2 else 3 * p ** 4) * 8.0 * nrhs
+    flops_exec = info["flops_fwd"] * nrhs    # as executed (sum factorisation shares work)
     steps = plan.steps()
     pairs = {t: a * b for t, a, b in plan.stages()}
-    bytes_ = sum(pairs[t + 1] + pairs[t - lev + 1] for t, lev in steps) * PD * 8.0
+    bytes_ = sum(pairs[t + 1] + pairs[t - lev + 1] for t, lev in steps) * PD * 8.0 * nrhs
     level_s = float(np.mean(level_ms)) * 1e-3
     per_launch_s = level_s / S
     hbm_peak, hbm_src = peaks()
@@ -380,7 +385,8 @@ def main_bfly(args, rank, world, dist):
     main, alt = (roof_alu, roof_hbm) if roof_alu["frac"] >= roof_hbm["frac"] else (roof_hbm, roof_alu)
     main["traffic"] = traffic
     alt["traffic"] = traffic
-    main["kernel"] = (f"level_kernel<float,{d},{p}> (recursive step, {S} launches of "
+    main["kernel"] = (("level_tc_kernel<" if prec == "tc" else "level_kernel<float,") + f"{d},{p}> "
+                      f"(recursive step, {S} launches of "
                       + "/".join(str(lev) for _, lev in steps) + " stages)")
     main["algorithmic_per_launch"] = {"flops": flops / S, "bytes": bytes_ / S,
                                       "executed_flops": flops_exec / S}
@@ -392,16 +398,18 @@ def main_bfly(args, rank, world, dist):
                   + ["final"])
     out["kernel_ms"] = {n: float(v) for n, v in zip(kern_names, kern_ms.mean(axis=0))}
 
-    value = replica_value(world, ms)
+    value = replica_value(world, ms) * nrhs   # right-hand sides transformed per second
     line = {
         "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {**describe(inst), "parallelism": f"replicas{world}" if world > 1 else "single GPU",
-                   "precision": "FP32 applies, FP64-built operators and weights"},
+        "config": {**describe(inst, nrhs), "parallelism": f"replicas{world}" if world > 1 else "single GPU",
+                   "precision": "FP32 applies, FP64-built operators and weights" if prec == "fp32" else
+                   "recursive step on the tensor cores (TF32 operands split hi + lo, FP32 accumulation), "
+                   "FP32 leaf and final steps"},
         "effective_IJ_per_s": value * nx * nk,
-        "e2e": {"value": world / e2e_s, "unit": "transforms/s", "h2d_bytes_per_step": nk * 8,
-                "d2h_bytes_per_step": nx * 8, "ms": e2e_s * 1e3,
+        "e2e": {"value": world * nrhs / e2e_s, "unit": "transforms/s", "h2d_bytes_per_step": nk * 8 * nrhs,
+                "d2h_bytes_per_step": nx * 8 * nrhs, "ms": e2e_s * 1e3,
                 "call": "bfly_execute_host (pinned host buffers)"},
         "roofline": main,
         "adjoint": {"ms": float(np.mean(adj_ms)), "transforms_per_s": 1e3 / float(np.mean(adj_ms)),
@@ -428,7 +436,8 @@ def main_bfly(args, rank, world, dist):
             except Exception as exc:  # recorded in the line; the headline stands
                 line[key] = {"error": f"{type(exc).__name__}: {exc}"}
     if not args.no_baselines:
-        rate, m, thr, dt = oracle_direct_rate(inst, f_np.astype(np.complex128), args.cpu_seconds)
+        f_one = f_np if nrhs == 1 else f_np[0]
+        rate, m, thr, dt = oracle_direct_rate(inst, f_one.astype(np.complex128), args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "transforms/s", "cores": thr, "kind": "oracle",
                                 "sample": f"FP64 direct sum (eq. 1.1) over {m} of {nx} targets "
                                           f"(seeded), all {nk} sources, {dt:.1f} s, "
@@ -616,6 +625,7 @@ def main_batch(args):
     import torch
     from paper_0801_1524_gb300 import workloads as w
     from paper_0801_1524_gb300.plan import Plan
+    args.nrhs = args.nrhs or 16
     insts = w.star_batch(nrhs=args.nrhs)
     dev = torch.device("cuda", 0)
     smem_kb, stages, tuned = 0, 0, None
