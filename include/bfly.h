@@ -164,9 +164,12 @@ bfly_status bfly_execute_adjoint(bfly_plan_t plan, const void *u, void *f, int n
 
 /*
  * bfly_execute_host — bfly_execute (adjoint = 0) or bfly_execute_adjoint (adjoint = 1)
- * on HOST buffers: copies the input to the plan's device staging buffer, runs the sweep,
- * copies the result back and waits for it.  Pinned host memory gives asynchronous copies;
- * pageable memory works too.  in: [nrhs][nk] (forward) or [nrhs][nx] (adjoint).
+ * on HOST buffers, returning once the result is in out_host.  When both buffers are
+ * pinned (page-locked, e.g. cudaHostAlloc or cudaHostRegister) the leaf step reads the
+ * input and the final step writes the result directly in host memory through their
+ * device mappings (no staging copies); otherwise the input is copied to the plan's device
+ * staging buffer, the sweep runs, and the result is copied back.  in: [nrhs][nk]
+ * (forward) or [nrhs][nx] (adjoint).
  */
 bfly_status bfly_execute_host(bfly_plan_t plan, const void *in_host, void *out_host,
                               int nrhs, int dtype, int adjoint, void *stream);

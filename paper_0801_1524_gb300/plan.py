@@ -26,10 +26,24 @@ def _dtype_code(t):
     raise TypeError(f"expected complex64 or complex128, got {t.dtype}")
 
 
+_raw_stream = None
+
+
 def _stream_ptr(stream):
+    """cudaStream_t of `stream` (a torch.cuda.Stream, a raw handle as int, or None for the
+    current stream of the current device)."""
+    global _raw_stream
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
     torch = _torch()
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return ctypes.c_void_p(s.cuda_stream)
+    if stream is not None:
+        return ctypes.c_void_p(stream.cuda_stream)
+    if _raw_stream is None:
+        # the current stream's handle without building a Stream object on every call
+        fn = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+        _raw_stream = (lambda: fn(torch.cuda.current_device())) if fn else \
+            (lambda: torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(_raw_stream())
 
 
 class Plan:
@@ -258,17 +272,26 @@ class Plan:
     # ---- execution on host buffers (copies inside the call)
     def execute_host(self, v: np.ndarray, adjoint: bool = False, out: np.ndarray | None = None,
                      stream=None) -> np.ndarray:
-        v2 = np.ascontiguousarray(np.atleast_2d(v))
+        v = np.asarray(v)
+        one = v.ndim == 1
+        v2 = v.reshape(1, -1) if one else v
+        if not v2.flags.c_contiguous:
+            v2 = np.ascontiguousarray(v2)
         n_in, n_out = (self.nx, self.nk) if adjoint else (self.nk, self.nx)
-        if v2.shape[1] != n_in or v2.dtype not in (np.complex64, np.complex128):
+        dt = v2.dtype
+        if v2.shape[1] != n_in or (dt != np.complex64 and dt != np.complex128):
             raise ValueError(f"input must be complex64/complex128 [nrhs, {n_in}]")
         if out is None:
-            out = np.empty((v2.shape[0], n_out), dtype=v2.dtype)
-        code = native.BFLY_C128 if v2.dtype == np.complex128 else native.BFLY_C64
-        native.check(self._lib.bfly_execute_host(self._h, v2.ctypes.data, out.ctypes.data,
-                                                 v2.shape[0], code, int(adjoint),
-                                                 _stream_ptr(stream)), "bfly_execute_host")
-        return out[0] if np.ndim(v) == 1 else out
+            out = np.empty((v2.shape[0], n_out), dtype=dt)
+        elif out.dtype != dt or out.size != v2.shape[0] * n_out or not out.flags.c_contiguous:
+            raise ValueError("out must be contiguous [nrhs, n] of the input's dtype")
+        st = self._lib.bfly_execute_host(self._h, v2.__array_interface__["data"][0],
+                                         out.__array_interface__["data"][0], v2.shape[0],
+                                         native.BFLY_C128 if dt == np.complex128 else native.BFLY_C64,
+                                         int(adjoint), _stream_ptr(stream))
+        if st != native.BFLY_OK:
+            native.check(st, "bfly_execute_host")
+        return out.reshape(-1) if one and out.ndim == 2 else out
 
 
 class Batch:
