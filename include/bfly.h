@@ -77,7 +77,7 @@ typedef struct {
   int max_nrhs;            /* workspace is sized for up to this many right-hand sides (>= 1) */
   unsigned flags;          /* BFLY_FLAG_* */
   int smem_kb;             /* shared memory per block for the recursive step, 0 = default
-                              (55 KB in 2D, 73 KB in 3D; 110 KB for BFLY_PREC_TC) */
+                              (2D: 72 KB FP32, 55 KB FP64; 3D: 73 KB; BFLY_PREC_TC: 110 KB) */
   const char *tune_cache;  /* autotuning cache file (text), or NULL */
   int stages;              /* at most this many stages per launch of the recursive step:
                               2D 1..3 (0 = default 3), 3D 1..2 (0 = default 1; larger

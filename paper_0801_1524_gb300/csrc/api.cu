@@ -216,9 +216,11 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   // capacities: the largest chunk that fits the shared-memory budget of one block
   // default budget: four blocks per SM in 2D; in 3D (8x larger tiles at p = 5) fewer,
   // larger blocks, whose chunks hold enough tiles to keep the consumer warps busy
-  // (tensor-core step: eight right-hand sides per tile slot, two blocks per SM)
-  const size_t want =
-      (size_t)(o.smem_kb > 0 ? o.smem_kb : o.prec == BFLY_PREC_TC ? 110 : (dim == 3 ? 73 : 55)) * 1024;
+  // (2D FP32: 72 KB, three blocks per SM, the autotuner's choice on the curve, star and
+  // batched workloads; tensor-core step: eight right-hand sides per tile slot, two blocks
+  // per SM)
+  const int def_kb = o.prec == BFLY_PREC_TC ? 110 : dim == 3 ? 73 : o.prec == BFLY_PREC_FP64 ? 55 : 72;
+  const size_t want = (size_t)(o.smem_kb > 0 ? o.smem_kb : def_kb) * 1024;
   auto caps_for = [&](size_t budget) {
     // tile slots in steps of 8 (FP32, FP64); of 1 for the tensor-core step, whose slots hold
     // eight right-hand sides each

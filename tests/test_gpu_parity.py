@@ -247,3 +247,44 @@ def test_execute_host_on_pinned_buffers(prec, dt):
     assert torch.equal(g_pin, P.adjoint(u_pin.to("cuda")).cpu())
     # pageable buffers take the staging copies: the same results
     assert np.array_equal(P.execute_host(f_pin.numpy().copy()), u_pin.numpy())
+
+
+@pytest.mark.parametrize("dim,N,n,p", [(2, 2.0 ** 20, 120, 5), (2, 2.0 ** 16 + 0.5, 100, 7), (3, 2.0 ** 10, 60, 3),
+                                       (2, 2.0 ** 30, 40, 3)])
+def test_deep_trees(dim, N, n, p):
+    # few points in a large domain: up to 30 levels, mostly single-box stages, every
+    # launch of the recursive step with a handful of chunks
+    # The oracle forms its phases 2 pi x.k/N from absolute coordinates (|x|, |k| <= N), so
+    # its own FP64 rounding is about N eps relative (2.4e-7 at N = 2^30); the CUDA path
+    # forms no phase beyond a unit leaf (exact offsets, operators independent of N).  The
+    # FP64 comparison allows that rounding on top of the 1e-9 gate.
+    inst = w.small_random(dim, N, p, n, n, 17, edge_fraction=0.2)
+    f = inst.sources()[0]
+    ref = ob.butterfly(inst.x, inst.k, f, N, p)
+    u64 = _fwd(inst, f, "fp64")
+    assert rel_l2(u64, ref) < TOL64 + 4 * N * np.finfo(float).eps
+    assert rel_l2(_fwd(inst, f, "fp32", torch.complex64), ref) < tol32(p)
+    assert rel_l2(_fwd(inst, f, "fp32", torch.complex64), u64) < tol32(p)
+
+
+def test_coincident_points():
+    # repeated targets and sources (the same coordinates several times, some on box edges)
+    rng = np.random.default_rng(21)
+    N = 256.0
+    base_x = w.random_points(60, N, 2, 22, edge_fraction=0.3)
+    base_k = w.random_points(50, N, 2, 23, edge_fraction=0.3)
+    x = base_x[rng.integers(0, 60, 400)]
+    k = base_k[rng.integers(0, 50, 300)]
+    inst = w.Instance("dup", 2, N, 7, x, k)
+    f = inst.sources()[0]
+    ref = ob.butterfly(x, k, f, N, 7)
+    u64 = _fwd(inst, f, "fp64")
+    assert rel_l2(u64, ref) < TOL64
+    assert rel_l2(_fwd(inst, f, "fp32", torch.complex64), ref) < tol32(7)
+    # equal targets get equal potentials
+    first = {}
+    for i, row in enumerate(map(tuple, x)):
+        if row in first:
+            assert u64[i] == u64[first[row]]
+        else:
+            first[row] = i
