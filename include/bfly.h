@@ -214,15 +214,22 @@ bfly_status bfly_execute_events(bfly_plan_t plan, const void *in, void *out, int
  *   t        a stage at a launch boundary of the plan: L, or the last stage of one of the
  *            launches of bfly_plan_step (plans built with stages = 1 have every stage);
  *            otherwise BFLY_ERR_INVALID_ARG.
- * bfly_execute_to_stage   f device [nrhs][nk] (dtype) -> charges of stage t.
- * bfly_execute_from_stage charges of stage t -> u device [nrhs][nx] (dtype).
- * bfly_execute_to_stage(t = 0) followed by bfly_execute_from_stage(t = 0) is bfly_execute.
+ * bfly_execute_to_stage   adjoint = 0: f device [nrhs][nk] (dtype) -> the leaf step and
+ *                         the recursive step down to stage t -> charges of stage t;
+ *                         adjoint = 1: u device [nrhs][nx] -> the final step's transpose and
+ *                         the adjoint sweep from stage 0 up to stage t -> charges of stage t.
+ * bfly_execute_from_stage adjoint = 0: charges of stage t -> the rest of the sweep and the
+ *                         final step -> u device [nrhs][nx] (dtype);
+ *                         adjoint = 1: charges of stage t -> the adjoint sweep up to stage L
+ *                         and the leaf step's transpose -> f device [nrhs][nk].
+ * to_stage(t) followed by from_stage(t) is bfly_execute (adjoint = 0) or
+ * bfly_execute_adjoint (adjoint = 1), for every t at a launch boundary.
  * Asynchronous on `stream`; they copy the stage through the plan's charge buffers.
  */
-bfly_status bfly_execute_to_stage(bfly_plan_t plan, const void *f, int t, void *charges, int nrhs, int dtype,
-                                  void *stream);
-bfly_status bfly_execute_from_stage(bfly_plan_t plan, const void *charges, int t, void *u, int nrhs, int dtype,
-                                    void *stream);
+bfly_status bfly_execute_to_stage(bfly_plan_t plan, const void *in, int t, void *charges, int nrhs, int dtype,
+                                  int adjoint, void *stream);
+bfly_status bfly_execute_from_stage(bfly_plan_t plan, const void *charges, int t, void *out, int nrhs, int dtype,
+                                    int adjoint, void *stream);
 
 /*
  * bfly_execute_noalloc — bfly_execute (forward, device buffers) without any allocation:

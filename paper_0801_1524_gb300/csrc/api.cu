@@ -652,10 +652,10 @@ bfly_status check_stage(bfly_plan_t P, int t, const void *charges, int *b) {
 
 extern "C" {
 
-bfly_status bfly_execute_to_stage(bfly_plan_t plan, const void *f, int t, void *charges, int nrhs, int dtype,
-                                  void *stream) {
+bfly_status bfly_execute_to_stage(bfly_plan_t plan, const void *in, int t, void *charges, int nrhs, int dtype,
+                                  int adjoint, void *stream) {
   g_err.clear();
-  bfly_status st = check_split(plan, f, plan ? plan->nk : 0, nrhs, dtype);
+  bfly_status st = check_split(plan, in, plan ? (adjoint ? plan->nx : plan->nk) : 0, nrhs, dtype);
   if (st != BFLY_OK) return st;
   int b = 0;
   st = check_stage(plan, t, charges, &b);
@@ -663,40 +663,62 @@ bfly_status bfly_execute_to_stage(bfly_plan_t plan, const void *f, int t, void *
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const bool io64 = dtype == BFLY_C128;
   const size_t bytes = (size_t)nrhs * plan->pairs[t] * plan->TS * plan->elem_bytes;
-  if (plan->nk == 0 || plan->nx == 0) {  // no sources: zero charges; no targets: no tiles
+  const int L = plan->L, S = (int)plan->steps.size();
+  if (plan->nk == 0 || plan->nx == 0) {  // an empty side: zero charges, or no tiles at all
     if (bytes) BFLY_CUDA(cudaMemsetAsync(charges, 0, bytes, s));
     return BFLY_OK;
   }
-  BFLY_CUDA(plan->ks->spread(point_args(plan, false, f, plan->buf[0], nrhs, io64, false,
-                                        plan->pairs[plan->L] * plan->TS), s));
-  for (int si = 0; si < b; ++si)
-    BFLY_CUDA(plan->ks->level(level_args(plan, si, false, nrhs), false, plan->level_grid, plan->level_smem, s));
+  if (!adjoint) {
+    // leaf step, then the launches from boundary 0 (stage L) to boundary b (stage t)
+    BFLY_CUDA(plan->ks->spread(point_args(plan, false, in, plan->buf[0], nrhs, io64, false,
+                                          plan->pairs[L] * plan->TS), s));
+    for (int si = 0; si < b; ++si)
+      BFLY_CUDA(plan->ks->level(level_args(plan, si, false, nrhs), false, plan->level_grid, plan->level_smem, s));
+  } else {
+    // the final step's transpose, then the adjoint launches from boundary S (stage 0) back
+    // to boundary b (stage t)
+    BFLY_CUDA(plan->ks->spread(point_args(plan, true, in, plan->buf[S & 1], nrhs, io64, true,
+                                          plan->pairs[0] * plan->TS), s));
+    for (int si = S - 1; si >= b; --si)
+      BFLY_CUDA(plan->ks->level(level_args(plan, si, true, nrhs), true, plan->level_grid, plan->level_smem, s));
+  }
   if (bytes) BFLY_CUDA(cudaMemcpyAsync(charges, plan->buf[b & 1], bytes, cudaMemcpyDeviceToDevice, s));
   return BFLY_OK;
 }
 
-bfly_status bfly_execute_from_stage(bfly_plan_t plan, const void *charges, int t, void *u, int nrhs, int dtype,
-                                    void *stream) {
+bfly_status bfly_execute_from_stage(bfly_plan_t plan, const void *charges, int t, void *out, int nrhs, int dtype,
+                                    int adjoint, void *stream) {
   g_err.clear();
-  bfly_status st = check_split(plan, u, plan ? plan->nx : 0, nrhs, dtype);
+  const int64_t n_out = plan ? (adjoint ? plan->nk : plan->nx) : 0, n_in = plan ? (adjoint ? plan->nx : plan->nk) : 0;
+  bfly_status st = check_split(plan, out, n_out, nrhs, dtype);
   if (st != BFLY_OK) return st;
   int b = 0;
   st = check_stage(plan, t, charges, &b);
   if (st != BFLY_OK) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const bool io64 = dtype == BFLY_C128;
-  if (plan->nx == 0) return BFLY_OK;
-  if (plan->nk == 0) {
-    BFLY_CUDA(cudaMemsetAsync(u, 0, (size_t)nrhs * plan->nx * (io64 ? 16 : 8), s));
+  const int L = plan->L, S = (int)plan->steps.size();
+  if (n_out == 0) return BFLY_OK;
+  if (n_in == 0) {
+    BFLY_CUDA(cudaMemsetAsync(out, 0, (size_t)nrhs * n_out * (io64 ? 16 : 8), s));
     return BFLY_OK;
   }
   const size_t bytes = (size_t)nrhs * plan->pairs[t] * plan->TS * plan->elem_bytes;
-  const int S = (int)plan->steps.size();
   if (bytes) BFLY_CUDA(cudaMemcpyAsync(plan->buf[b & 1], charges, bytes, cudaMemcpyDeviceToDevice, s));
-  for (int si = b; si < S; ++si)
-    BFLY_CUDA(plan->ks->level(level_args(plan, si, false, nrhs), false, plan->level_grid, plan->level_smem, s));
-  BFLY_CUDA(plan->ks->interp(point_args(plan, true, plan->buf[S & 1], u, nrhs, io64, false,
-                                        plan->pairs[0] * plan->TS), s));
+  if (!adjoint) {
+    // the launches from boundary b to boundary S (stage 0), then the final step
+    for (int si = b; si < S; ++si)
+      BFLY_CUDA(plan->ks->level(level_args(plan, si, false, nrhs), false, plan->level_grid, plan->level_smem, s));
+    BFLY_CUDA(plan->ks->interp(point_args(plan, true, plan->buf[S & 1], out, nrhs, io64, false,
+                                          plan->pairs[0] * plan->TS), s));
+  } else {
+    // the adjoint launches from boundary b back to boundary 0 (stage L), then the leaf
+    // step's transpose
+    for (int si = b - 1; si >= 0; --si)
+      BFLY_CUDA(plan->ks->level(level_args(plan, si, true, nrhs), true, plan->level_grid, plan->level_smem, s));
+    BFLY_CUDA(plan->ks->interp(point_args(plan, false, plan->buf[0], out, nrhs, io64, true,
+                                          plan->pairs[L] * plan->TS), s));
+  }
   return BFLY_OK;
 }
 

@@ -48,8 +48,8 @@ SIGNATURES = {
     "bfly_plan_destroy": (None, [_vp]),
     "bfly_execute": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "bfly_execute_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
-    "bfly_execute_to_stage": (_i, [_vp, _vp, _i, _vp, _i, _i, _vp]),
-    "bfly_execute_from_stage": (_i, [_vp, _vp, _i, _vp, _i, _i, _vp]),
+    "bfly_execute_to_stage": (_i, [_vp, _vp, _i, _vp, _i, _i, _i, _vp]),
+    "bfly_execute_from_stage": (_i, [_vp, _vp, _i, _vp, _i, _i, _i, _vp]),
     "bfly_execute_adjoint": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
     "bfly_execute_host": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
     "bfly_direct": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),

@@ -219,11 +219,13 @@ class Plan:
         last stage of every recursive-step launch."""
         return [self.info()["L"]] + [t - lev + 1 for t, lev in self.steps()]
 
-    def to_stage(self, f, t: int, out=None, stream=None):
-        """bfly_execute_to_stage: the leaf step and the recursive step down to stage t;
-        returns the stage-t charges [nrhs, nA * nB * TS] (plan precision, plan tile order)."""
+    def to_stage(self, v, t: int, out=None, adjoint: bool = False, stream=None):
+        """bfly_execute_to_stage: forward, the leaf step and the recursive step down to stage
+        t of sources v [nrhs, nk]; adjoint, the final step's transpose and the adjoint sweep
+        up to stage t of potentials v [nrhs, nx].  Returns the stage-t charges
+        [nrhs, nA * nB * TS] (plan precision, plan tile order)."""
         torch = _torch()
-        s, _ = self._prep(f, self.nk, "f")
+        s, _ = self._prep(v, self.nx if adjoint else self.nk, "v")
         nA, nB = self.stages()[t][1:]
         pd = self.p ** self.dim
         ts = pd if self._charge_dtype() == torch.complex128 else pd + (pd & 1)
@@ -233,22 +235,23 @@ class Plan:
             raise ValueError("charges must be contiguous [nrhs, nA * nB * TS] of the plan's precision")
         native.check(self._lib.bfly_execute_to_stage(self._h, ctypes.c_void_p(s.data_ptr()), int(t),
                                                      ctypes.c_void_p(out.data_ptr()), s.shape[0],
-                                                     _dtype_code(s), _stream_ptr(stream)), "bfly_execute_to_stage")
+                                                     _dtype_code(s), int(adjoint), _stream_ptr(stream)),
+                     "bfly_execute_to_stage")
         return out
 
-    def from_stage(self, charges, t: int, out=None, dtype=None, stream=None):
-        """bfly_execute_from_stage: stage-t charges -> potentials [nrhs, nx] (dtype: the
-        charges' complex type unless given)."""
+    def from_stage(self, charges, t: int, out=None, dtype=None, adjoint: bool = False, stream=None):
+        """bfly_execute_from_stage: stage-t charges -> forward, potentials [nrhs, nx];
+        adjoint, sources [nrhs, nk] (dtype: the charges' complex type unless given)."""
         torch = _torch()
         c = charges.contiguous()
         if c.dtype != self._charge_dtype():
             raise ValueError("charges must have the plan's precision")
         nrhs = c.shape[0]
         if out is None:
-            out = torch.empty((nrhs, self.nx), dtype=dtype or c.dtype, device=c.device)
+            out = torch.empty((nrhs, self.nk if adjoint else self.nx), dtype=dtype or c.dtype, device=c.device)
         native.check(self._lib.bfly_execute_from_stage(self._h, ctypes.c_void_p(c.data_ptr()), int(t),
                                                        ctypes.c_void_p(out.data_ptr()), nrhs, _dtype_code(out),
-                                                       _stream_ptr(stream)), "bfly_execute_from_stage")
+                                                       int(adjoint), _stream_ptr(stream)), "bfly_execute_from_stage")
         return out
 
     def adjoint(self, u, out=None, stream=None):

@@ -20,7 +20,10 @@ of A.  So
 
 ShardLayout is the host-side partition (from a host-only plan of all points);
 pack/assemble/exchange_p2p are the exchange; ShardedTransform runs one rank on its GPU
-(bfly_execute_to_stage, the exchange, bfly_execute_from_stage).
+(bfly_execute_to_stage, the exchange, bfly_execute_from_stage).  The adjoint runs the same
+way backwards: the ranks of T_X boxes take their targets up to stage t_mid, the exchange
+is transposed (pack_adjoint/assemble_adjoint: blocks split in B, joined in A), and the
+ranks of T_K boxes finish with the leaf step's transpose for their sources.
 """
 from __future__ import annotations
 
@@ -115,6 +118,19 @@ def assemble(layout: ShardLayout, rank: int, received):
     return torch.cat(list(received), dim=2).contiguous()
 
 
+def pack_adjoint(layout: ShardLayout, rank: int, charges):
+    """The adjoint sweep's blocks of rank `rank`: charges [nrhs, nA_r, nB (all of level
+    t_mid), TS] -> for every rank q the columns B of q's boxes, [nrhs, nA_r, nB_q, TS]."""
+    return [charges[:, :, layout.kb[q]:layout.kb[q + 1]].contiguous() for q in range(layout.world)]
+
+
+def assemble_adjoint(layout: ShardLayout, rank: int, received):
+    """Rank `rank`'s stage-t_mid input of the adjoint sweep: the blocks [nrhs, nA_q, nB_r,
+    TS] of every rank q side by side in A -> [nrhs, nA (all of level a0), nB_r, TS]."""
+    import torch
+    return torch.cat(list(received), dim=1).contiguous()
+
+
 def exchange_p2p(sends, recv_shapes, rank: int, world: int, dist, group=None):
     """Point-to-point exchange: sends[q] goes to rank q, the block from rank q (shape
     recv_shapes[q]) is returned at position q; the own block is kept in place."""
@@ -174,3 +190,25 @@ class ShardedTransform:
         got = exchange_p2p(pack(self.layout, self.rank, c), self.recv_shapes(c.shape[0]), self.rank,
                            self.layout.world, dist, group)
         return self.lower(assemble(self.layout, self.rank, got))
+
+    # ---- the adjoint (the exact conjugate transpose: the sweep run backwards, T_X to T_K)
+    def upper_adjoint(self, u_local):
+        """Stage-t_mid charges of the adjoint sweep from this rank's targets (the final
+        step's transpose and the adjoint sweep up to t_mid), [nrhs, nA_r, nB, TS]."""
+        L = self.layout
+        c = self.lo.to_stage(u_local, L.t_mid, adjoint=True)
+        return c.reshape(c.shape[0], L.n_xboxes(self.rank), len(L.kboxes), self.ts)
+
+    def lower_adjoint(self, charges, out=None):
+        """This rank's sources from its stage-t_mid input of the adjoint [nrhs, nA, nB_r, TS]."""
+        return self.up.from_stage(charges.reshape(charges.shape[0], -1), self.layout.t_mid, out=out, adjoint=True)
+
+    def recv_shapes_adjoint(self, nrhs):
+        L = self.layout
+        return [(nrhs, L.n_xboxes(q), L.n_kboxes(self.rank), self.ts) for q in range(L.world)]
+
+    def adjoint(self, u_local, dist, group=None):
+        c = self.upper_adjoint(u_local)
+        got = exchange_p2p(pack_adjoint(self.layout, self.rank, c), self.recv_shapes_adjoint(c.shape[0]),
+                           self.rank, self.layout.world, dist, group)
+        return self.lower_adjoint(assemble_adjoint(self.layout, self.rank, got))

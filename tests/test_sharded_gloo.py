@@ -5,6 +5,9 @@ chunk programs, executed by the numpy interpreter of test_step_programs with the
 operators of the method), exchanges the middle stage with the other rank through the
 module's pack / exchange_p2p / assemble, runs the rest of the sweep for its targets, and
 must reproduce the stage-0 charges of the unsharded sweep for its targets' leaves.  The
+adjoint runs backwards the same way (the conjugate-transposed operators on the adjoint
+programs, the exchange transposed by pack_adjoint / assemble_adjoint) and must reproduce
+the unsharded adjoint sweep's stage-L charges for each rank's source leaves.  The
 partition itself is checked too: every point on exactly one rank, each rank's boxes a
 contiguous run of the Morton order."""
 import os
@@ -88,6 +91,62 @@ def _rank(rank, world, port, case, out):
     out.put((rank, g0, leaves, lay.t_mid, [len(s) for s in lay.sources], [len(t) for t in lay.targets]))
 
 
+def _run_steps_adjoint(P, x, opsH, first, last):
+    """The plan's adjoint launches first - 1, .., last on the tiles x (interpreter)."""
+    import test_step_programs as tsp
+    pairs = {t: a * b for t, a, b in P.stages()}
+    steps = P.steps()
+    for s in range(first - 1, last - 1, -1):
+        t, lev = steps[s]
+        x = tsp.run_program(P.program(s, True), P.dim, P.p, x, pairs[t + 1], opsH)
+    return x
+
+
+def _stage0_tiles(P, L, seed, shape):
+    """Seeded stage-0 tiles (T_X leaves x the T_K root) in the order of P's T_X leaves,
+    drawn per leaf box so that every plan of a subset of the targets sees the same tile."""
+    out = []
+    for b in P.boxes("x", L):
+        rng = np.random.default_rng([seed] + [int(v) for v in b])
+        out.append(rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+    return np.array(out).reshape((-1,) + shape)
+
+
+def _rank_adjoint(rank, world, port, case, out):
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, HERE)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    import test_step_programs as tsp
+    from paper_0801_1524_gb300 import sharded
+    from paper_0801_1524_gb300 import workloads as w
+    from paper_0801_1524_gb300.plan import Plan
+    dim, N, p, nx, nk, seed, stages = case
+    inst = w.small_random(dim, N, p, nx, nk, seed, edge_fraction=0.2)
+    opsH = np.conj(np.transpose(tsp._method_ops(p), (0, 2, 1)))
+    lay = sharded.ShardLayout(inst.x, inst.k, N, p, world, stages=stages)
+    pd = p ** dim
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # first part of the adjoint: this rank's targets, stage 0 -> t_mid
+        lo = Plan(inst.x[lay.targets[rank]], inst.k, N, p, host_only=True, stages=stages)
+        g0 = _stage0_tiles(lo, lay.L, 99, (p,) * dim)
+        c = _run_steps_adjoint(lo, g0, opsH, len(lo.steps()), lo.boundaries().index(lay.t_mid))
+        c = torch.as_tensor(c.reshape(1, lay.n_xboxes(rank), len(lay.kboxes), pd))
+        sends = [torch.view_as_real(b) for b in sharded.pack_adjoint(lay, rank, c)]
+        shapes = [(1, lay.n_xboxes(q), lay.n_kboxes(rank), pd, 2) for q in range(world)]
+        got = sharded.exchange_p2p(sends, shapes, rank, world, dist)
+        cin = sharded.assemble_adjoint(lay, rank, [torch.view_as_complex(g.contiguous()) for g in got])
+        # second part: this rank's sources, t_mid -> stage L
+        up = Plan(inst.x, inst.k[lay.sources[rank]], N, p, host_only=True, stages=stages)
+        gL = _run_steps_adjoint(up, cin.numpy().reshape((-1,) + (p,) * dim), opsH, up.boundaries().index(lay.t_mid), 0)
+        leaves = up.boxes("k", lay.L)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+    out.put((rank, gL, leaves))
+
+
 CASES = [(2, 128.0, 5, 500, 400, 1, 0), (2, 200.5, 7, 400, 350, 2, 0), (2, 256.0, 5, 600, 500, 3, 1),
          (3, 16.0, 3, 300, 260, 4, 0)]
 
@@ -149,3 +208,36 @@ def test_layout_partitions_points_into_contiguous_runs():
             pos = {tuple(b): i for i, b in enumerate(lay.kboxes)}
             ii = np.array([pos[tuple(b)] for b in bx])
             assert ii.min() >= lay.kb[r] and ii.max() < lay.kb[r + 1]
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[3]])
+def test_two_gloo_ranks_reproduce_the_unsharded_adjoint_sweep(case):
+    sys.path.insert(0, HERE)
+    import test_step_programs as tsp
+    from paper_0801_1524_gb300 import workloads as w
+    from paper_0801_1524_gb300.plan import Plan
+    dim, N, p, nx, nk, seed, stages = case
+    world = 2
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_adjoint, args=(r, world, port, case, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    res = sorted((q.get(timeout=300) for _ in procs), key=lambda v: v[0])
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    inst = w.small_random(dim, N, p, nx, nk, seed, edge_fraction=0.2)
+    P = Plan(inst.x, inst.k, N, p, host_only=True, stages=stages)
+    L = P.info()["L"]
+    opsH = np.conj(np.transpose(tsp._method_ops(p), (0, 2, 1)))
+    ref = tsp.sweep(P, _stage0_tiles(P, L, 99, (p,) * dim), opsH, adjoint=True)
+    col = {tuple(b): i for i, b in enumerate(P.boxes("k", L))}
+    scale = np.abs(ref).max()
+    seen = set()
+    for rank, gL, leaves in res:
+        idx = np.array([col[tuple(b)] for b in leaves])
+        seen |= set(idx.tolist())
+        assert np.abs(gL - ref[idx]).max() / scale < 1e-12, rank
+    assert seen == set(range(len(col)))
