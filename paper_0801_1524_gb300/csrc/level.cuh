@@ -287,6 +287,7 @@ __device__ __forceinline__ void run_pass(const Item *items, int n_items, int n_t
     const int fl = st * 32 + lane;
     if (fl >= nfib) continue;
     const int ti = fl / FIB, f = fl - ti * FIB;
+    __builtin_assume(f >= 0 && f < FIB);  // the fibre's offsets below then need no division
     const Item it = items[ti];
     const int base = (f / SK) * SK * P + (f % SK);
     C y[P];

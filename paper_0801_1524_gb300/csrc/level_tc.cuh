@@ -153,6 +153,7 @@ __device__ __forceinline__ void run_pass_tc(const Item *items, int n_items, int 
 #pragma unroll 1
   for (int u = u0; u < u1; ++u) {
     const int ti = u / FIB, fb = u - ti * FIB;
+    __builtin_assume(fb >= 0 && fb < FIB);
     const Item it = items[ti];
     const int base = (fb / SK) * SK * P + (fb % SK);
     const int op0 = it.ops & 3, op1 = (it.ops >> 2) & 3;
