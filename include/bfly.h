@@ -352,7 +352,7 @@ bfly_status bfly_plan_stage(bfly_plan_t plan, int t, int64_t *nA, int64_t *nB);
 /* Message of the last failure on this thread ("" if none). */
 const char *bfly_last_error(void);
 
-/* Build identification, e.g. "bfly 0.1 sm_103a". */
+/* Build identification, e.g. "bfly 0.2 sm_103a". */
 const char *bfly_version(void);
 
 #ifdef __cplusplus

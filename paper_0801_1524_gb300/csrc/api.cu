@@ -101,7 +101,7 @@ extern "C" {
 
 const char *bfly_last_error(void) { return g_err.c_str(); }
 
-const char *bfly_version(void) { return "bfly 0.1 sm_103a"; }
+const char *bfly_version(void) { return "bfly 0.2 sm_103a"; }
 
 void bfly_plan_destroy(bfly_plan_t plan) {
   if (!plan) return;
