@@ -70,7 +70,7 @@ def test_star_batch_full_size():
     from paper_0801_1524_gb300.plan import Batch, Plan
     insts = w.star_batch(nrhs=16)
     out = {}
-    for prec, dtype in (("fp32", torch.complex64), ("fp64", torch.complex128)):
+    for prec, dtype in (("fp32", torch.complex64), ("tc", torch.complex64), ("fp64", torch.complex128)):
         plans = [Plan(I.x, I.k, I.N, I.p, precision=prec, max_nrhs=16) for I in insts]
         batch = Batch(plans)
         fs = [torch.as_tensor(I.sources(), device="cuda").to(dtype) for I in insts]
@@ -81,15 +81,17 @@ def test_star_batch_full_size():
                 batch.forward(fs, us, stream=side)
         side.synchronize()
         assert batch.device_status() == 0
-        if prec == "fp32":
+        if prec != "fp64":
             # every instance equals its own plan's transform (the same chunk arithmetic)
             for P, f, u in zip(plans, fs, us):
                 assert torch.equal(u, P.forward(f))
         out[prec] = [u.to(torch.complex128).cpu().numpy() for u in us]
         del batch, plans
-    # FP32 against FP64 on every instance and right-hand side
-    worst = max(rel_l2(a[r], b[r]) for a, b in zip(out["fp32"], out["fp64"]) for r in range(16))
-    assert worst < 1e-6, worst
+    # FP32 (multiply-adds) and the tensor-core path against FP64 on every instance and
+    # right-hand side
+    for prec in ("fp32", "tc"):
+        worst = max(rel_l2(a[r], b[r]) for a, b in zip(out[prec], out["fp64"]) for r in range(16))
+        assert worst < 1e-6, (prec, worst)
     # the two smallest instances against the oracle's butterfly, all 16 right-hand sides
     for i in sorted(range(len(insts)), key=lambda i: insts[i].N)[:2]:
         I = insts[i]

@@ -14,11 +14,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def test_bounded_wait_reports_timeout_and_context_survives():
+@pytest.mark.parametrize("prec", ["fp32", "tc"])
+def test_bounded_wait_reports_timeout_and_context_survives(prec):
     from paper_0801_1524_gb300.plan import Plan
     inst = w.small_random(2, 64.0, 5, 400, 400, 31)
     f = inst.sources()[0]
-    stalled = Plan(inst.x, inst.k, inst.N, inst.p, flags=native.BFLY_FLAG_TEST_STALL)
+    stalled = Plan(inst.x, inst.k, inst.N, inst.p, precision=prec, flags=native.BFLY_FLAG_TEST_STALL)
     stalled.forward(torch.as_tensor(f, device="cuda"))
     bits = stalled.device_status()
     assert bits & 4, bits            # the compute warps gave up waiting for their data

@@ -27,7 +27,8 @@ def _call_noalloc(plan, f, u):
                                     1 if f.dim() == 1 else f.shape[0], dtype, stream)
 
 
-@pytest.mark.parametrize("prec,dtype,tol", [("fp32", torch.complex64, 1e-6), ("fp64", torch.complex128, 1e-9)])
+@pytest.mark.parametrize("prec,dtype,tol", [("fp32", torch.complex64, 1e-6), ("fp64", torch.complex128, 1e-9),
+                                            ("tc", torch.complex64, 1e-6)])
 def test_noalloc_matches_execute_on_two_calls(prec, dtype, tol):
     from paper_0801_1524_gb300.plan import Plan
     N, p = 1024.0, 7
