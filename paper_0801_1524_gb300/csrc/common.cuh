@@ -54,6 +54,11 @@ __device__ __forceinline__ C cadd(C a, C b) {
   a.y += b.y;
   return a;
 }
+// FP32: one paired addition (add.rn.f32x2), rounded like the two scalar ones
+template <>
+__device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+  return __fadd2_rn(a, b);
+}
 // The value of lane (lane ^ mask) of the warp (all lanes take part).
 template <typename C>
 __device__ __forceinline__ C shfl_xor_c(C a, int mask) {
