@@ -528,7 +528,8 @@ def run_batch(insts, nrhs, steps32, steps64, warmup, dev, flush, smem_kb=0, prec
     runs = [(pr, torch.complex64, steps32) for pr in precisions] + [("fp64", torch.complex128, steps64)]
     for prec, dtype, steps in runs:
         plans = [Plan(I.x, I.k, I.N, I.p, precision=prec, max_nrhs=nrhs,
-                      smem_kb=smem_kb if prec != "fp64" else 0, stages=stages if prec != "fp64" else 0)
+                      smem_kb=smem_kb if prec == precisions[0] else 0,
+                      stages=stages if prec == precisions[0] else 0)
                  for I in insts]
         batch = Batch(plans)
         fs = [torch.as_tensor(I.sources(dtype=np.complex64, nrhs=nrhs), device=dev).to(dtype) for I in insts]
@@ -578,11 +579,13 @@ def batch_summary(args, dev, flush):
     (N log-uniform in [512, 16384], as drawn), p = 7, 16 complex64 right-hand sides each."""
     from paper_0801_1524_gb300 import workloads as w
     insts = w.star_batch(nrhs=16)
-    r = run_batch(insts, 16, steps32=10, steps64=2, warmup=2, dev=dev, flush=flush, precisions=("fp32", "tc"))
+    r = run_batch(insts, 16, steps32=10, steps64=2, warmup=2, dev=dev, flush=flush,
+                  precisions=("fp32", "fp32g", "tc"))
     r["workload"] = ("star_batch: 64 instances, N log-uniform in 512..16384 (sum N = %.0f), p=7, "
-                     "16 complex64 RHS each, graph replay; FP32 (paired FP32 multiply-adds) and TC "
-                     "(tensor cores, 3xTF32) batches against the FP64 batch" % sum(I.N for I in insts))
-    for prec in ("fp32", "tc"):
+                     "16 complex64 RHS each, graph replay; FP32 (paired FP32 multiply-adds), FP32G (the same with "
+                     "right-hand sides in groups of eight) and TC (tensor cores, TF32 x 4) batches against the "
+                     "FP64 batch" % sum(I.N for I in insts))
+    for prec in ("fp32", "fp32g", "tc"):
         r[prec]["instance_rhs_per_s"] = len(insts) * 16 * 1e3 / r[prec]["ms"]
     return r
 
@@ -641,7 +644,8 @@ def main_batch(args):
         t0 = time.perf_counter()
         info = Plan(big.x, big.k, big.N, big.p, max_nrhs=args.nrhs, autotune=True).info()
         names = {0: "fp64", 1: "fp32", 2: "tc"}
-        smem_kb, stages, precs = info["smem_kb"], info["stages_per_launch"], (names[info["prec"]],)
+        prec = "fp32g" if info["rhs_groups"] else names[info["prec"]]
+        smem_kb, stages, precs = info["smem_kb"], info["stages_per_launch"], (prec,)
         tuned = {"smem_kb": smem_kb, "stages_per_launch": stages, "precision": precs[0],
                  "tuned_on": f"largest instance (N = {big.N:.0f})", "tuning_s": time.perf_counter() - t0}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)

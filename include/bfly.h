@@ -62,15 +62,24 @@ typedef enum { BFLY_PREC_FP64 = 0, BFLY_PREC_FP32 = 1, BFLY_PREC_TC = 2 } bfly_p
  * forward sweep of each with max_nrhs right-hand sides (median of three after a warm-up),
  * and keep the fastest.  Candidates: the shared-memory budget per block (which sets how
  * many tiles, and so box pairs, one block takes at a time and how many blocks share an
- * SM) x the stages per launch (2D: 3, 2, 1; 3D: 1, 2); and, for an FP32 plan in 2D with
- * max_nrhs >= 8, the tensor-core recursive step (BFLY_PREC_TC) at two budgets and two
- * stage counts.  With tune_cache set, a choice recorded there for the same GPU, dim, p,
+ * SM) x the stages per launch (2D: 3, 2, 1; 3D: one); for an FP32 plan in 2D with
+ * max_nrhs >= 4, the right-hand-side grouped step (BFLY_FLAG_RHS_GROUPS) at two budgets
+ * and two stage counts; with max_nrhs >= 8 also the tensor-core recursive step
+ * (BFLY_PREC_TC) at two budgets and two stage counts.  With tune_cache set, a choice recorded there for the same GPU, dim, p,
  * requested precision, nrhs and size class is reused, and new choices are appended.
- * bfly_plan_info_t reports the chosen precision, budget and stages. */
+ * bfly_plan_info_t reports the chosen precision, budget, stages and whether the
+ * right-hand sides are grouped (rhs_groups). */
 #define BFLY_FLAG_AUTOTUNE 4u
 /* One stage per launch of the recursive step also in 2D (no stages fused in shared
  * memory): the unfused programs of Sec. 2.2 step 3, for comparison and testing. */
 #define BFLY_FLAG_ONE_STAGE 8u
+/* FP32 plans in 2D: the recursive step takes the right-hand sides eight at a time (each
+ * work item a chunk x eight right-hand sides, tiles right-hand side major in shared
+ * memory, a 32-lane step four fibres x eight right-hand sides) with the same paired FP32
+ * multiply-adds, in the same order, as the default kernel: the same results, a layout
+ * with fewer shared-memory bank conflicts for many right-hand sides.  Default budget
+ * 110 KB per block. */
+#define BFLY_FLAG_RHS_GROUPS 16u
 
 typedef struct {
   int prec;                /* bfly_precision; default BFLY_PREC_FP32 */
@@ -108,6 +117,7 @@ typedef struct {
   int steps;                    /* launches of the recursive step per transform: up to three
                                    stages each in 2D, one in 3D (bfly_plan_step) */
   int stages_per_launch;        /* the most stages of one launch the plan was built for */
+  int rhs_groups;               /* 1 when built with BFLY_FLAG_RHS_GROUPS */
 } bfly_plan_info_t;
 
 /*

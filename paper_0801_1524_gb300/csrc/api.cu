@@ -139,6 +139,10 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     return fail(BFLY_ERR_INVALID_ARG, "unknown precision");
   if (o.prec == BFLY_PREC_TC && dim != 2)
     return fail(BFLY_ERR_UNSUPPORTED, "the tensor-core recursive step is built for dim = 2");
+  // right-hand-side groups: the FP32 recursive step on groups of eight right-hand sides
+  const bool rhs_groups = o.prec == BFLY_PREC_FP32 && (o.flags & BFLY_FLAG_RHS_GROUPS);
+  if (rhs_groups && dim != 2)
+    return fail(BFLY_ERR_UNSUPPORTED, "the right-hand-side grouped recursive step is built for dim = 2");
   if (o.max_nrhs < 1 || o.max_nrhs > 4096) return fail(BFLY_ERR_INVALID_ARG, "max_nrhs must be in 1..4096");
   if (o.reserved != 0) return fail(BFLY_ERR_INVALID_ARG, "reserved options must be zero");
   if (o.stages < 0 || o.stages > bfly::kMaxLevels) return fail(BFLY_ERR_INVALID_ARG, "stages must be in 0..3");
@@ -195,7 +199,7 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
 
   const bool host_only = (o.flags & BFLY_FLAG_HOST_ONLY) != 0;
   // shared memory plan of the recursive step
-  P->ks = select_kernels(p, o.prec == BFLY_PREC_FP64 ? 0 : o.prec == BFLY_PREC_TC ? 2 : 1, dim);
+  P->ks = select_kernels(p, o.prec == BFLY_PREC_FP64 ? 0 : o.prec == BFLY_PREC_TC ? 2 : rhs_groups ? 3 : 1, dim);
   if (!P->ks) {
     delete P;
     return fail(BFLY_ERR_UNSUPPORTED, "no kernels for this (dim, p)");
@@ -219,12 +223,12 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   // (2D FP32: 72 KB, three blocks per SM, the autotuner's choice on the curve, star and
   // batched workloads; tensor-core step: eight right-hand sides per tile slot, two blocks
   // per SM)
-  const int def_kb = o.prec == BFLY_PREC_TC ? 110 : dim == 3 ? 73 : o.prec == BFLY_PREC_FP64 ? 55 : 72;
+  const int def_kb = (o.prec == BFLY_PREC_TC || rhs_groups) ? 110 : dim == 3 ? 73 : o.prec == BFLY_PREC_FP64 ? 55 : 72;
   const size_t want = (size_t)(o.smem_kb > 0 ? o.smem_kb : def_kb) * 1024;
   auto caps_for = [&](size_t budget) {
     // tile slots in steps of 8 (FP32, FP64); of 1 for the tensor-core step, whose slots hold
     // eight right-hand sides each
-    const int step = o.prec == BFLY_PREC_TC ? 1 : 8;
+    const int step = (o.prec == BFLY_PREC_TC || rhs_groups) ? 1 : 8;
     for (int cap = 1024; cap >= step; cap -= step) {
       const ChunkCaps c{cap, cap, cap, P->ks->meta_bytes(cap, cap, cap)};
       if (P->ks->level_smem(c) <= budget) return c;
@@ -280,6 +284,7 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     for (int i = 0; i < L / max_lev; ++i) todo.push_back(max_lev);
   }
   I.stages_per_launch = max_lev;
+  I.rhs_groups = rhs_groups ? 1 : 0;
   // the programs of the planned steps, forward and adjoint, compiled on all host cores
   // (each is independent); a step split after a capacity failure is compiled below
   struct Compiled {
@@ -834,7 +839,7 @@ std::string tune_key(int dim, int p, int prec, int nrhs, int64_t max_pairs) {
 // One configuration of the recursive step: shared-memory budget per block, stages per
 // launch (2D), precision of the applies.
 struct TuneChoice {
-  int smem_kb = 0, stages = 0, prec = -1;
+  int smem_kb = 0, stages = 0, prec = -1, groups = 0;  // groups: BFLY_FLAG_RHS_GROUPS
 };
 
 // The last choice recorded for `key` ("<key> <smem_kb> [<stages> <prec>]" lines), or
@@ -849,9 +854,10 @@ TuneChoice cache_lookup(const char *path, const std::string &key) {
     std::string l(line);
     if (l.compare(0, key.size(), key) != 0 || l.size() <= key.size() || l[key.size()] != ' ') continue;
     TuneChoice c;
-    const int n = std::sscanf(l.c_str() + key.size(), " %d %d %d", &c.smem_kb, &c.stages, &c.prec);
+    const int n = std::sscanf(l.c_str() + key.size(), " %d %d %d %d", &c.smem_kb, &c.stages, &c.prec, &c.groups);
     if (n >= 1 && c.smem_kb > 0) {
       if (n < 3) c.stages = 0, c.prec = -1;
+      if (n < 4) c.groups = 0;
       found = c;
     }
   }
@@ -863,7 +869,7 @@ void cache_store(const char *path, const std::string &key, const TuneChoice &c) 
   if (!path) return;
   FILE *fh = std::fopen(path, "a");
   if (!fh) return;
-  std::fprintf(fh, "%s %d %d %d\n", key.c_str(), c.smem_kb, c.stages, c.prec);
+  std::fprintf(fh, "%s %d %d %d %d\n", key.c_str(), c.smem_kb, c.stages, c.prec, c.groups);
   std::fclose(fh);
 }
 
@@ -910,6 +916,8 @@ bfly_status autotune_create(bfly_plan_t *out, int dim, double N, int64_t nx, con
     r.smem_kb = c.smem_kb;
     if (c.stages > 0) r.stages = c.stages;
     if (c.prec >= 0) r.prec = c.prec;
+    if (c.groups) r.flags |= BFLY_FLAG_RHS_GROUPS;
+    else r.flags &= ~BFLY_FLAG_RHS_GROUPS;
     return r;
   };
   const TuneChoice cached = cache_lookup(o.tune_cache, key);
@@ -926,6 +934,11 @@ bfly_status autotune_create(bfly_plan_t *out, int dim, double N, int64_t nx, con
       if (fixed_stages && stg != (o.stages > 0 ? o.stages : 1)) continue;
       for (int kb : {40, 55, 73, 110}) cands.push_back({kb, stg, o.prec});
     }
+    if (o.prec == BFLY_PREC_FP32 && o.max_nrhs >= 4)
+      for (int stg : {3, 2}) {
+        if (fixed_stages && stg != (o.stages > 0 ? o.stages : 1)) continue;
+        for (int kb : {110, 220}) cands.push_back({kb, stg, BFLY_PREC_FP32, 1});
+      }
     if (o.prec == BFLY_PREC_FP32 && o.max_nrhs >= 8)
       for (int stg : {3, 1}) {
         if (fixed_stages && stg != (o.stages > 0 ? o.stages : 1)) continue;

@@ -103,8 +103,9 @@ bfly_status bfly_batch_create(bfly_batch_t *out, int count, const bfly_plan_t *p
   for (int i = 0; i < count; ++i) {
     bfly_plan_t P = plans[i];
     if (!P || !P->dmem) return set_error(BFLY_ERR_INVALID_ARG, "every plan must be a device plan");
-    if (P->dim != P0->dim || P->p != P0->p || P->prec != P0->prec || P->device != P0->device)
-      return set_error(BFLY_ERR_INVALID_ARG, "plans of a batch share dim, p, precision and device");
+    if (P->dim != P0->dim || P->p != P0->p || P->prec != P0->prec || P->device != P0->device || P->ks != P0->ks)
+      return set_error(BFLY_ERR_INVALID_ARG,
+                       "plans of a batch share dim, p, precision, device and recursive-step kernel");
     if (P->caps.cap0 != P0->caps.cap0 || P->caps.cap1 != P0->caps.cap1 || P->caps.max_out != P0->caps.max_out)
       return set_error(BFLY_ERR_INVALID_ARG, "plans of a batch share their shared-memory tile capacities");
   }

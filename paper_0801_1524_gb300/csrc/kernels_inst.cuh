@@ -198,14 +198,15 @@ struct Impl {
   }
 };
 
-// The FP32 kernel set with the recursive step on the tensor cores (level_tc_kernel): the
-// leaf and final steps and the charge layout are those of the FP32 set.
-template <int D, int P>
+// The FP32 kernel sets with the recursive step on groups of eight right-hand sides
+// (level_tc_kernel): on the tensor cores (MMA) or with paired FP32 multiply-adds; the leaf
+// and final steps and the charge layout are those of the FP32 set.
+template <int D, int P, bool MMA>
 struct ImplTc {
   using S = TcShape<D, P>;
   static cudaError_t level(const LevelArgs &a, bool adjoint, int grid, size_t smem, cudaStream_t s) {
     if (a.nchunks <= 0) return cudaSuccess;
-    return launch_dependent(adjoint ? level_tc_kernel<D, P, true> : level_tc_kernel<D, P, false>, dim3(grid),
+    return launch_dependent(adjoint ? level_tc_kernel<D, P, true, MMA> : level_tc_kernel<D, P, false, MMA>, dim3(grid),
                             dim3(kLevelThreads), smem, s, a);
   }
   static cudaError_t level_setup(size_t smem, int *blocks) {
@@ -214,15 +215,15 @@ struct ImplTc {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(level_tc_kernel<D, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    e = cudaFuncSetAttribute(level_tc_kernel<D, P, false, MMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(level_tc_kernel<D, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess) e = init_tc_operators();
+      e = cudaFuncSetAttribute(level_tc_kernel<D, P, true, MMA>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e == cudaSuccess) e = MMA ? init_tc_operators() : init_operators<float>();
     if (e != cudaSuccess) return e;
     int b2 = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, level_tc_kernel<D, P, false>, kLevelThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, level_tc_kernel<D, P, false, MMA>, kLevelThreads, smem);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, level_tc_kernel<D, P, true>, kLevelThreads, smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, level_tc_kernel<D, P, true, MMA>, kLevelThreads, smem);
     if (b2 < *blocks) *blocks = b2;
     return e;
   }
@@ -240,7 +241,8 @@ struct ImplTc {
 #define BFLY_CAT2(a, b) a##b
 #define BFLY_CAT(a, b) BFLY_CAT2(a, b)
 const KernelSet *BFLY_CAT(kernels_p, BFLY_P)(int prec, int dim) {
-  if (prec == 2) return dim == 2 ? ImplTc<2, BFLY_P>::get() : nullptr;
+  if (prec == 2) return dim == 2 ? ImplTc<2, BFLY_P, true>::get() : nullptr;
+  if (prec == 3) return dim == 2 ? ImplTc<2, BFLY_P, false>::get() : nullptr;
   if (dim == 2) return prec == 0 ? Impl<double, 2, BFLY_P>::get() : Impl<float, 2, BFLY_P>::get();
   if (dim == 3) return prec == 0 ? Impl<double, 3, BFLY_P>::get() : Impl<float, 3, BFLY_P>::get();
   return nullptr;

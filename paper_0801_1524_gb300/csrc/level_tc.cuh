@@ -194,11 +194,86 @@ __device__ __forceinline__ void run_pass_tc(const Item *items, int n_items, int 
   }
 }
 
+// Pass K of the consumer warps with paired FP32 multiply-adds on the same right-hand-side
+// grouped layout (BFLY_FLAG_RHS_GROUPS): a 32-lane step takes four fibres x the eight
+// right-hand sides of the group (lane = 8 * fibre + right-hand side), each lane applying
+// the factored operators to its fibre exactly as level_kernel's run_pass does (the same
+// multiply-adds in the same order, so the results equal level_kernel's).  With the
+// right-hand sides rs = 4 (mod 32) floats apart, the two fibres of a half-warp fall on
+// disjoint banks whenever their element offsets differ in parity (consecutive fibres of a
+// tile), where level_kernel's lanes (one fibre each, tile slots data dependent) conflict
+// on about half of the wavefronts; the chunk's program and runs are read once per eight
+// right-hand sides.
+template <int D, int P, int K, bool ADJ>
+__device__ __forceinline__ void run_pass_rg(const Item *items, int n_items, int n_two, const float *src,
+                                            int src_rs, float *dst, int dst_rs, int nr, int warp, int lane) {
+  using C = float2;
+  using S = TcShape<D, P>;
+  constexpr int FIB = S::FIB, TS = S::TS;
+  constexpr int SK = ipow(P, D - 1 - K);
+  constexpr int FPS = 32 / kTcRhs;  // fibres per step
+  const int nfib = n_items * FIB, nfib2 = n_two * FIB;
+  const int steps = (nfib + FPS - 1) / FPS, steps2 = (nfib2 + FPS - 1) / FPS;
+  const int total = steps + steps2;
+  const int per = (total + kConsumerWarps - 1) / kConsumerWarps;
+  const int w0 = min(total, warp * per), w1 = min(total, w0 + per);
+  auto first_step = [&](int w) { return w <= 2 * steps2 ? (w + 1) / 2 : w - steps2; };
+  const int s0 = first_step(w0), s1 = first_step(w1);
+  const int rr = lane & (kTcRhs - 1), fsub = lane / kTcRhs;
+  if (rr >= nr) return;  // a partial group: these lanes have no right-hand side
+  const C *srcr = reinterpret_cast<const C *>(src + (size_t)rr * src_rs);
+  C *dstr = reinterpret_cast<C *>(dst + (size_t)rr * dst_rs);
+#pragma unroll 1
+  for (int st = s0; st < s1; ++st) {
+    const int fl = st * FPS + fsub;
+    if (fl >= nfib) continue;
+    const int ti = fl / FIB, f = fl - ti * FIB;
+    __builtin_assume(f >= 0 && f < FIB);
+    const Item it = items[ti];
+    const int base = (f / SK) * SK * P + (f % SK);
+    C y[P];
+#pragma unroll
+    for (int m = 0; m < P; ++m) y[m] = make_float2(0.0f, 0.0f);
+    const C *X0 = srcr + (size_t)it.src0 * TS + base;
+    const bool d0 = (it.ops & 1) != 0, g0 = (it.ops & 2) != 0;
+    if (fl < nfib2) {
+      const C *X1 = srcr + (size_t)it.src1 * TS + base;
+      if constexpr (!ADJ) {
+        apply_factored<float, P, SK, ADJ, 0>(g0, X0, y);
+        apply_factored<float, P, SK, ADJ, 1>(g0, X1, y);
+      } else if (d0) {
+        apply_factored<float, P, SK, ADJ, 1>(true, X1, y);
+        apply_factored<float, P, SK, ADJ, 1>(false, X0, y);
+      } else {
+        apply_factored<float, P, SK, ADJ, 0>(true, X1, y);
+        apply_factored<float, P, SK, ADJ, 0>(false, X0, y);
+      }
+    } else if (d0) {
+      apply_factored<float, P, SK, ADJ, 1>(g0, X0, y);
+    } else {
+      apply_factored<float, P, SK, ADJ, 0>(g0, X0, y);
+    }
+    C *Y = dstr + (size_t)it.dst * TS + base;
+#pragma unroll
+    for (int m = 0; m < P; ++m) Y[m * SK] = y[m];
+  }
+}
+
+template <bool MMA, int D, int P, int K, bool ADJ>
+__device__ __forceinline__ void run_pass_group(const Item *items, int n_items, int n_two, const float *src,
+                                               int src_rs, float *dst, int dst_rs, int nr, int warp, int lane) {
+  if constexpr (MMA)
+    run_pass_tc<D, P, K, ADJ>(items, n_items, n_two, src, src_rs, dst, dst_rs, nr, warp, lane);
+  else
+    run_pass_rg<D, P, K, ADJ>(items, n_items, n_two, src, src_rs, dst, dst_rs, nr, warp, lane);
+}
+
 // The persistent, warp-specialised kernel of level_kernel with work items (chunk, group
 // of eight right-hand sides): the producer copies every right-hand side of the group run
-// by run, the consumers run the passes on the tensor cores.
-template <int D, int P, bool ADJ>
-__global__ void __launch_bounds__(kLevelThreads, 2) level_tc_kernel(const LevelArgs a) {
+// by run, the consumers run the passes on the tensor cores (MMA) or with paired FP32
+// multiply-adds (run_pass_rg).
+template <int D, int P, bool ADJ, bool MMA>
+__global__ void __launch_bounds__(kLevelThreads, MMA ? 2 : 3) level_tc_kernel(const LevelArgs a) {
   using S = TcShape<D, P>;
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char *ptr = smem;
@@ -377,16 +452,16 @@ __global__ void __launch_bounds__(kLevelThreads, 2) level_tc_kernel(const LevelA
     const int nr = *reinterpret_cast<const volatile int *>(end_it + 1 + s);
     for (int j = 0; j < NP; j += D) {
       if (j > 0) consumer_sync();
-      run_pass_tc<D, P, 0, ADJ>(ip, hdr[4 + j], hdr[4 + kMaxPasses + j], (j & 1) ? scr : in_s, (j & 1) ? rs1 : rs0,
+      run_pass_group<MMA, D, P, 0, ADJ>(ip, hdr[4 + j], hdr[4 + kMaxPasses + j], (j & 1) ? scr : in_s, (j & 1) ? rs1 : rs0,
                                 (j & 1) ? in_s : scr, (j & 1) ? rs0 : rs1, nr, warp, lane);
       ip += hdr[4 + j];
       consumer_sync();
-      run_pass_tc<D, P, 1, ADJ>(ip, hdr[5 + j], hdr[5 + kMaxPasses + j], (j & 1) ? in_s : scr, (j & 1) ? rs0 : rs1,
+      run_pass_group<MMA, D, P, 1, ADJ>(ip, hdr[5 + j], hdr[5 + kMaxPasses + j], (j & 1) ? in_s : scr, (j & 1) ? rs0 : rs1,
                                 (j & 1) ? scr : in_s, (j & 1) ? rs1 : rs0, nr, warp, lane);
       ip += hdr[5 + j];
       if constexpr (D == 3) {
         consumer_sync();
-        run_pass_tc<D, P, (D == 3 ? 2 : 0), ADJ>(ip, hdr[6 + j], hdr[6 + kMaxPasses + j], (j & 1) ? scr : in_s,
+        run_pass_group<MMA, D, P, (D == 3 ? 2 : 0), ADJ>(ip, hdr[6 + j], hdr[6 + kMaxPasses + j], (j & 1) ? scr : in_s,
                                                  (j & 1) ? rs1 : rs0, (j & 1) ? in_s : scr, (j & 1) ? rs0 : rs1, nr,
                                                  warp, lane);
         ip += hdr[6 + j];

@@ -16,6 +16,7 @@ BFLY_FLAG_HOST_ONLY = 1
 BFLY_FLAG_TEST_STALL = 2
 BFLY_FLAG_AUTOTUNE = 4
 BFLY_FLAG_ONE_STAGE = 8
+BFLY_FLAG_RHS_GROUPS = 16
 
 # Every function the header declares, with (restype, argtypes).
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -39,7 +40,7 @@ class PlanInfo(ctypes.Structure):
                 ("smem_kb", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("tuned_ms", ctypes.c_double),
                 ("plan_seconds", ctypes.c_double), ("steps", ctypes.c_int),
-                ("stages_per_launch", ctypes.c_int)]
+                ("stages_per_launch", ctypes.c_int), ("rhs_groups", ctypes.c_int)]
 
 
 SIGNATURES = {

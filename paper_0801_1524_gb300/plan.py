@@ -9,7 +9,10 @@ import numpy as np
 
 from . import native
 
-PRECISIONS = {"fp64": native.BFLY_PREC_FP64, "fp32": native.BFLY_PREC_FP32, "tc": native.BFLY_PREC_TC}
+# "fp32g": FP32 with the recursive step on groups of eight right-hand sides
+# (BFLY_FLAG_RHS_GROUPS; the same results as "fp32")
+PRECISIONS = {"fp64": native.BFLY_PREC_FP64, "fp32": native.BFLY_PREC_FP32, "tc": native.BFLY_PREC_TC,
+              "fp32g": native.BFLY_PREC_FP32}
 
 
 def _torch():
@@ -74,7 +77,8 @@ class Plan:
         opts.prec = PRECISIONS[precision]
         opts.max_nrhs = self.max_nrhs
         opts.flags = ((native.BFLY_FLAG_HOST_ONLY if host_only else 0) |
-                      (native.BFLY_FLAG_AUTOTUNE if autotune else 0) | int(flags))
+                      (native.BFLY_FLAG_AUTOTUNE if autotune else 0) |
+                      (native.BFLY_FLAG_RHS_GROUPS if precision == "fp32g" else 0) | int(flags))
         opts.smem_kb = int(smem_kb)
         opts.stages = int(stages)
         self._tune_cache = tune_cache.encode() if tune_cache else None

@@ -23,7 +23,8 @@ PREC = {native.BFLY_PREC_FP32: "fp32", native.BFLY_PREC_TC: "tc", native.BFLY_PR
 
 def _chosen(plan):
     i = plan.info()
-    return dict(smem_kb=i["smem_kb"], stages=i["stages_per_launch"], precision=PREC[i["prec"]])
+    prec = "fp32g" if i["rhs_groups"] else PREC[i["prec"]]
+    return dict(smem_kb=i["smem_kb"], stages=i["stages_per_launch"], precision=prec)
 
 
 @pytest.mark.parametrize("nrhs", [2, 16])
