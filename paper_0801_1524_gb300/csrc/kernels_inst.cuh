@@ -182,13 +182,13 @@ struct Impl {
     const int64_t work = a.nbox * PD;
     if (work == 0) return cudaSuccess;
     constexpr int64_t E = kPointThreads * kSpreadPerThread;
-    dim3 grid((unsigned)((work + E - 1) / E), (unsigned)a.nrhs);
+    dim3 grid((unsigned)((work + E - 1) / E), (unsigned)((a.nrhs + kPointRhs - 1) / kPointRhs));
     return launch_dependent(spread_kernel<R, D, P>, grid, dim3(kPointThreads), 0, s, a);
   }
   static cudaError_t interp(const PointArgs &a, cudaStream_t s) {
     if (a.n_total == 0) return cudaSuccess;
     const int64_t lanes = a.n_total * kInterpLanes;
-    dim3 grid((unsigned)((lanes + kPointThreads - 1) / kPointThreads), (unsigned)a.nrhs);
+    dim3 grid((unsigned)((lanes + kPointThreads - 1) / kPointThreads), (unsigned)((a.nrhs + kPointRhs - 1) / kPointRhs));
     return launch_dependent(interp_kernel<R, D, P>, grid, dim3(kPointThreads), 0, s, a);
   }
   static const KernelSet *get() {

@@ -26,6 +26,8 @@ constexpr int kSpreadPerThread = 4;  // tile elements per thread
 // perm, weight rows) in shared memory, a batch at a time, so that every point is read
 // from memory once and the loads of a batch are in flight together; then each thread sums
 // the batch's points of its elements' leaves.
+constexpr int kPointRhs = 4;  // right-hand sides per block (leaf step) or lane group (final step)
+
 template <typename R, int D, int P>
 __global__ void __launch_bounds__(kPointThreads, 4) spread_kernel(const PointArgs a) {
   using C = typename Cx<R>::T;
@@ -35,20 +37,20 @@ __global__ void __launch_bounds__(kPointThreads, 4) spread_kernel(const PointArg
   __shared__ C s_w[BATCH][D * P];
   const int64_t n_el = a.nbox * PD;
   const int64_t e0 = (int64_t)blockIdx.x * E;
-  const int r = blockIdx.y;
+  // right-hand sides r0 .. r0 + nb - 1 of this block: the weights, leaf ranges and
+  // permutation are read once for all of them
+  const int r0 = blockIdx.y * kPointRhs, nb = min(kPointRhs, a.nrhs - r0);
   // element k of this thread: tile element l (< PD) of leaf bk (the plan's leaves number
   // fewer than 2^31), its points j0 .. j1 - 1 in sorted order
-  int bk[kSpreadPerThread], lt[kSpreadPerThread], j0[kSpreadPerThread], j1[kSpreadPerThread];
-  C acc[kSpreadPerThread];
+  // (the leaf's point range is read where it is used, an L1 hit, so that fewer values stay
+  // live across the right-hand sides)
+  int bk[kSpreadPerThread], lt[kSpreadPerThread];
 #pragma unroll
   for (int k = 0; k < kSpreadPerThread; ++k) {
     const int64_t w = e0 + threadIdx.x + k * kPointThreads;
     const bool on = w < n_el;
     bk[k] = on ? (int)(w / PD) : -1;
     lt[k] = on ? (int)(w - (int64_t)bk[k] * PD) : 0;
-    j0[k] = on ? a.leaf_start[bk[k]] : 0;
-    j1[k] = on ? a.leaf_start[bk[k] + 1] : 0;
-    acc[k] = cmk((R)0, (R)0);
   }
   pdl_trigger();
   // the block's points: those of leaves e0/PD .. (last element)/PD.  The leaf ranges, the
@@ -60,9 +62,10 @@ __global__ void __launch_bounds__(kPointThreads, 4) spread_kernel(const PointArg
   const C *W = reinterpret_cast<const C *>(a.W);
   constexpr int PJ = (BATCH + kPointThreads - 1) / kPointThreads;
   bool waited = false;
-  for (int pb = jb0; pb < jb1; pb += BATCH) {
-    const int n = min(BATCH, jb1 - pb);
-    int pj[PJ];
+  C acc[kSpreadPerThread];
+  int pj[PJ];
+  // stages the weights and permutation entries of points pb .. pb + n - 1
+  auto stage_plan = [&](int pb, int n) {
 #pragma unroll
     for (int q = 0; q < PJ; ++q) {
       const int t = threadIdx.x + q * kPointThreads;
@@ -72,10 +75,10 @@ __global__ void __launch_bounds__(kPointThreads, 4) spread_kernel(const PointArg
       const C wv = W[(size_t)pb * D * P + t];
       s_w[t / (D * P)][t % (D * P)] = a.conj ? cconj(wv) : wv;
     }
-    if (!waited) {
-      pdl_wait();
-      waited = true;
-    }
+  };
+  // gathers the values of right-hand side r of points pb .., then (after a barrier) adds
+  // their terms to the accumulators
+  auto accumulate = [&](int pb, int n, int r) {
 #pragma unroll
     for (int q = 0; q < PJ; ++q) {
       const int t = threadIdx.x + q * kPointThreads;
@@ -84,7 +87,8 @@ __global__ void __launch_bounds__(kPointThreads, 4) spread_kernel(const PointArg
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kSpreadPerThread; ++k) {
-      const int ja = max(j0[k], pb) - pb, jz = min(j1[k], pb + n) - pb;
+      if (bk[k] < 0) continue;
+      const int ja = max(a.leaf_start[bk[k]], pb) - pb, jz = min(a.leaf_start[bk[k] + 1], pb + n) - pb;
       // the index of element l along each axis (axis 0 slowest)
       int ld[D];
       int rem = lt[k];
@@ -101,13 +105,43 @@ __global__ void __launch_bounds__(kPointThreads, 4) spread_kernel(const PointArg
       }
     }
     __syncthreads();
-  }
-  if (!waited) pdl_wait();
+  };
+  auto store = [&](int r) {
 #pragma unroll
-  for (int k = 0; k < kSpreadPerThread; ++k)
-    if (bk[k] >= 0) {
-      reinterpret_cast<C *>(a.vout)[(size_t)r * a.tile_rhs + (size_t)bk[k] * a.tile_stride + lt[k]] = acc[k];
+    for (int k = 0; k < kSpreadPerThread; ++k)
+      if (bk[k] >= 0)
+        reinterpret_cast<C *>(a.vout)[(size_t)r * a.tile_rhs + (size_t)bk[k] * a.tile_stride + lt[k]] = acc[k];
+  };
+  if (jb1 - jb0 <= BATCH) {
+    // the usual case: the block's points fit one batch, staged once for every right-hand side
+    stage_plan(jb0, jb1 - jb0);
+    pdl_wait();
+    for (int q = 0; q < nb; ++q) {
+#pragma unroll
+      for (int k = 0; k < kSpreadPerThread; ++k) acc[k] = cmk((R)0, (R)0);
+      accumulate(jb0, jb1 - jb0, r0 + q);
+      store(r0 + q);
     }
+    return;
+  }
+  for (int q = 0; q < nb; ++q) {
+#pragma unroll
+    for (int k = 0; k < kSpreadPerThread; ++k) acc[k] = cmk((R)0, (R)0);
+    for (int pb = jb0; pb < jb1; pb += BATCH) {
+      const int n = min(BATCH, jb1 - pb);
+      stage_plan(pb, n);
+      if (!waited) {
+        pdl_wait();
+        waited = true;
+      }
+      accumulate(pb, n, r0 + q);
+    }
+    if (!waited) {
+      pdl_wait();
+      waited = true;
+    }
+    store(r0 + q);
+  }
 }
 
 constexpr int kInterpLanes = 8;  // lanes per target
@@ -115,53 +149,58 @@ constexpr int kInterpLanes = 8;  // lanes per target
 // val_i = sum_l prod_d W_i[d][l_d] tile[leaf(i)][l]   (conj(W) when a.conj)
 // Eight lanes per target: lane g sums the slices l_0 = g and g + 8 of the tile
 // (sum over l_1.. first, then the weight of l_0), and the eight partial sums are added
-// with shuffles; lane 0 writes the result in caller order.
+// with shuffles; lane 0 writes the result in caller order.  A lane group takes up to
+// kPointRhs right-hand sides of its target one after the other, reading the target's
+// weights, leaf and caller index once.
 template <typename R, int D, int P>
 __global__ void __launch_bounds__(kPointThreads) interp_kernel(const PointArgs a) {
   using C = typename Cx<R>::T;
   const int64_t gt = (int64_t)blockIdx.x * kPointThreads + threadIdx.x;
   const int64_t i = gt / kInterpLanes;
   const int g = (int)(gt % kInterpLanes);
-  const int r = blockIdx.y;
+  const int r0 = blockIdx.y * kPointRhs, nb = min(kPointRhs, a.nrhs - r0);
   const bool active = i < a.n_total;
-  C acc = cmk((R)0, (R)0);
   // the plan's weights and leaf indices are read before the predecessor grid has ended;
   // the tiles it writes after
   pdl_trigger();
   const C *Wi = reinterpret_cast<const C *>(a.W) + (size_t)(active ? i : 0) * D * P;
-  const C *tile = reinterpret_cast<const C *>(a.vin) + (size_t)r * a.tile_rhs +
-                  (size_t)(active ? a.point_leaf[i] : 0) * a.tile_stride;
+  const C *tile0 = reinterpret_cast<const C *>(a.vin) + (size_t)(active ? a.point_leaf[i] : 0) * a.tile_stride;
   C wl[P];  // weights of the last axis
 #pragma unroll
   for (int l = 0; l < P; ++l)
     wl[l] = !active ? cmk((R)0, (R)0) : a.conj ? cconj(Wi[(D - 1) * P + l]) : Wi[(D - 1) * P + l];
   pdl_wait();
-  if (active) {
+  for (int q = 0; q < nb; ++q) {
+    const int r = r0 + q;
+    const C *tile = tile0 + (size_t)r * a.tile_rhs;
+    C acc = cmk((R)0, (R)0);
+    if (active) {
 #pragma unroll
-    for (int h = 0; h < (P + kInterpLanes - 1) / kInterpLanes; ++h) {
-      const int l0 = g + h * kInterpLanes;
-      if (l0 >= P) break;
-      C s1 = cmk((R)0, (R)0);
-      if (D == 2) {
+      for (int h = 0; h < (P + kInterpLanes - 1) / kInterpLanes; ++h) {
+        const int l0 = g + h * kInterpLanes;
+        if (l0 >= P) break;
+        C s1 = cmk((R)0, (R)0);
+        if (D == 2) {
 #pragma unroll
-        for (int l1 = 0; l1 < P; ++l1) s1 = cfma(wl[l1], tile[l0 * P + l1], s1);
-      } else {
+          for (int l1 = 0; l1 < P; ++l1) s1 = cfma(wl[l1], tile[l0 * P + l1], s1);
+        } else {
 #pragma unroll 1
-        for (int l1 = 0; l1 < P; ++l1) {
-          C s2 = cmk((R)0, (R)0);
+          for (int l1 = 0; l1 < P; ++l1) {
+            C s2 = cmk((R)0, (R)0);
 #pragma unroll
-          for (int l2 = 0; l2 < P; ++l2) s2 = cfma(wl[l2], tile[(l0 * P + l1) * P + l2], s2);
-          const C w1 = a.conj ? cconj(Wi[P + l1]) : Wi[P + l1];
-          s1 = cfma(w1, s2, s1);
+            for (int l2 = 0; l2 < P; ++l2) s2 = cfma(wl[l2], tile[(l0 * P + l1) * P + l2], s2);
+            const C w1 = a.conj ? cconj(Wi[P + l1]) : Wi[P + l1];
+            s1 = cfma(w1, s2, s1);
+          }
         }
+        const C w0 = a.conj ? cconj(Wi[l0]) : Wi[l0];
+        acc = cfma(w0, s1, acc);
       }
-      const C w0 = a.conj ? cconj(Wi[l0]) : Wi[l0];
-      acc = cfma(w0, s1, acc);
     }
-  }
 #pragma unroll
-  for (int o = kInterpLanes / 2; o > 0; o /= 2) acc = cadd(acc, shfl_xor_c(acc, o));
-  if (active && g == 0) store_io(a.vout, (int64_t)r * a.n_total + a.perm[i], acc, a.io64);
+    for (int o = kInterpLanes / 2; o > 0; o /= 2) acc = cadd(acc, shfl_xor_c(acc, o));
+    if (active && g == 0) store_io(a.vout, (int64_t)r * a.n_total + a.perm[i], acc, a.io64);
+  }
 }
 
 // Plan-time weights, computed in FP64 and stored in the plan's precision R; tau is the
