@@ -80,6 +80,21 @@ typedef enum { BFLY_PREC_FP64 = 0, BFLY_PREC_FP32 = 1, BFLY_PREC_TC = 2 } bfly_p
  * with fewer shared-memory bank conflicts for many right-hand sides.  Default budget
  * 110 KB per block. */
 #define BFLY_FLAG_RHS_GROUPS 16u
+/* FP32 and FP64 plans: the whole recursive step of a transform (Sec. 2.2 step 3, stages
+ * L-1 .. 0) in one launch.  The chunks of all its steps form one list, step after step,
+ * and a block starts a chunk of a step as soon as the chunks of the step before it whose
+ * outputs it reads have written them (a flag per chunk and right-hand side in device
+ * memory, published with release and read with acquire semantics), instead of after the
+ * launch of the whole step before it has ended.  Every boundary between two steps has its
+ * own charge buffer: the plan holds steps - 1 more stage buffers than without the flag.
+ * bfly_execute, bfly_execute_adjoint, bfly_execute_host and bfly_execute_events run the
+ * sweep this way (bfly_execute_events then records its events between the recursive
+ * step's steps back to back, after the one launch); the split, no-allocation and batch
+ * entry points launch step by step as without the flag.  The results are bit-identical
+ * to those of the step-by-step launches.  BFLY_ERR_UNSUPPORTED with BFLY_PREC_TC or
+ * BFLY_FLAG_RHS_GROUPS; with BFLY_FLAG_AUTOTUNE, candidates on those steps are built
+ * without it. */
+#define BFLY_FLAG_DATAFLOW 32u
 
 typedef struct {
   int prec;                /* bfly_precision; default BFLY_PREC_FP32 */
@@ -118,6 +133,7 @@ typedef struct {
                                    stages each in 2D, one in 3D (bfly_plan_step) */
   int stages_per_launch;        /* the most stages of one launch the plan was built for */
   int rhs_groups;               /* 1 when built with BFLY_FLAG_RHS_GROUPS */
+  int dataflow;                 /* 1 when built with BFLY_FLAG_DATAFLOW */
 } bfly_plan_info_t;
 
 /*
@@ -268,7 +284,8 @@ bfly_status bfly_execute_noalloc(bfly_plan_t plan, const void *f, void *u, int n
  * bfly_device_status — waits for the device, then reads and clears the plan's device
  * status word.  Kernels whose bounded waits gave up set bits in it (1: the copy engine
  * side gave up waiting for a free buffer, 2: copies were still in flight at exit, 4: the
- * compute side gave up waiting for data) and return early.  *flags (optional) receives
+ * compute side gave up waiting for data, 8: a block of a BFLY_FLAG_DATAFLOW sweep gave up
+ * waiting for the outputs of other blocks) and return early.  *flags (optional) receives
  * the bits.  Returns BFLY_ERR_TIMEOUT when any bit was set, else BFLY_OK.
  */
 bfly_status bfly_device_status(bfly_plan_t plan, int *flags);

@@ -54,6 +54,7 @@ const KernelSet *select_kernels(int p, int prec, int dim) {
 
 #include "plan_state.hpp"
 
+using bfly_state::flow_args;
 using bfly_state::level_args;
 using bfly_state::point_args;
 
@@ -84,6 +85,164 @@ struct Arena {
 int levels_for(double N) {
   if (!(N > 1.0)) return 0;
   return (int)std::ceil(std::log2(N) - 1e-12);
+}
+
+// Output runs of chunk c of a compiled step program (read from its metadata blob).
+std::pair<const bfly::Run *, int> output_runs(const bfly::StageProgram &pg, size_t c) {
+  const unsigned char *bp = pg.blob.data() + pg.chunks[c].blob_off;
+  const int32_t *hdr = reinterpret_cast<const int32_t *>(bp);
+  int64_t n_items = 0;
+  for (int j = 0; j < hdr[0]; ++j) n_items += hdr[4 + j];
+  return {reinterpret_cast<const bfly::Run *>(bp + bfly::kBlobHeader + n_items * sizeof(bfly::Item)), hdr[2]};
+}
+
+// The single-launch sweep of one direction (flow step k: plan step k forward, S-1-k for
+// the adjoint).  Its entries are all chunks of all steps, step after step; a chunk of step
+// k reads tiles that chunks of step k-1 write (its sources), which come before it, as the
+// kernel's progress requires.  Returns an error message or "".
+std::string build_flow(bfly_plan_t P, bool adjoint, int blocks, bfly_plan_s::Flow &F) {
+  const int S = (int)P->steps.size();
+  F = bfly_plan_s::Flow{};
+  std::vector<const bfly::StageProgram *> pg(S);
+  std::vector<int64_t> in_tiles(S);
+  std::vector<int32_t> base(S + 1, 0);
+  for (int k = 0; k < S; ++k) {
+    const int s = adjoint ? S - 1 - k : k;
+    const bfly_plan_s::Step &st = P->steps[s];
+    pg[k] = adjoint ? &P->progA[s] : &P->progF[s];
+    in_tiles[k] = adjoint ? P->pairs[st.t - st.levels + 1] : P->pairs[st.t + 1];
+    base[k + 1] = base[k] + (int32_t)pg[k]->chunks.size();
+  }
+  const int32_t N = base[S];
+  std::vector<int32_t> src_off((size_t)N + 1, 0), src;  // sources of every node (node ids)
+  std::vector<int32_t> owner, d;
+  for (int k = 0; k < S; ++k) {
+    if (k > 0) {
+      owner.assign((size_t)in_tiles[k], -1);
+      for (size_t c = 0; c < pg[k - 1]->chunks.size(); ++c) {
+        const auto runs = output_runs(*pg[k - 1], c);
+        for (int j = 0; j < runs.second; ++j) {
+          const bfly::Run r = runs.first[j];
+          if (r.start < 0 || (int64_t)r.start + r.count > in_tiles[k]) return "output run outside its stage";
+          for (int q = 0; q < r.count; ++q) owner[(size_t)r.start + q] = base[k - 1] + (int32_t)c;
+        }
+      }
+    }
+    for (size_t c = 0; c < pg[k]->chunks.size(); ++c) {
+      const bfly::ChunkDesc &cd = pg[k]->chunks[c];
+      const int32_t n = base[k] + (int32_t)c;
+      d.clear();
+      for (int j = 0; k > 0 && j < cd.n_runs; ++j) {
+        const bfly::Run r = pg[k]->runs[(size_t)cd.run_off + j];
+        if (r.start < 0 || (int64_t)r.start + r.count > in_tiles[k]) return "input run outside its stage";
+        for (int q = 0; q < r.count; ++q) {
+          const int32_t o = owner[(size_t)r.start + q];
+          if (o < 0) return "an input tile that no chunk of the step before writes";
+          if (d.empty() || d.back() != o) d.push_back(o);
+        }
+      }
+      std::sort(d.begin(), d.end());
+      d.erase(std::unique(d.begin(), d.end()), d.end());
+      src.insert(src.end(), d.begin(), d.end());
+      src_off[(size_t)n + 1] = (int32_t)src.size();
+    }
+  }
+  // the order: step after step; within a step by the last of the chunk's sources in the
+  // launch's order, in groups of `blocks` (the chunks whose sources were taken early come
+  // first, for the blocks that reach the step while the step before it drains), the
+  // step's own order (decreasing work) within a group
+  std::vector<int32_t> order;
+  order.reserve((size_t)N);
+  std::vector<int32_t> pos((size_t)N, -1);
+  for (int k = 0; k < S; ++k) {
+    const int32_t n0 = base[k], n1 = base[k + 1];
+    std::vector<int32_t> step_nodes;
+    for (int32_t n = n0; n < n1; ++n) step_nodes.push_back(n);
+    std::vector<int64_t> key((size_t)(n1 - n0), 0);
+    for (int32_t n = n0; n < n1; ++n) {
+      int32_t last = -1;
+      for (int32_t j = src_off[n]; j < src_off[n + 1]; ++j) last = std::max(last, pos[src[j]]);
+      key[n - n0] = last < 0 ? 0 : last / std::max(blocks, 1);
+    }
+    std::stable_sort(step_nodes.begin(), step_nodes.end(),
+                     [&](int32_t x, int32_t y) { return key[x - n0] < key[y - n0]; });
+    for (int32_t n : step_nodes) {
+      pos[n] = (int32_t)order.size();
+      order.push_back(n);
+    }
+  }
+  // entries in that order
+  F.dep_off.assign(1, 0);
+  F.first_use.assign((size_t)N, -1);
+  F.nodes.reserve((size_t)N);
+  for (int32_t i = 0; i < N; ++i) {
+    const int32_t n = order[i];
+    const int k = (int)(std::upper_bound(base.begin(), base.end(), n) - base.begin()) - 1;
+    F.nodes.push_back({k, n - base[k]});
+    d.clear();
+    for (int32_t j = src_off[n]; j < src_off[n + 1]; ++j) d.push_back(pos[src[j]]);
+    std::sort(d.begin(), d.end());
+    for (int32_t x : d) {
+      if (x >= i) return "a chunk ordered before one of its sources";
+      if (F.first_use[x] < 0) F.first_use[x] = i;
+    }
+    F.dep_idx.insert(F.dep_idx.end(), d.begin(), d.end());
+    F.dep_off.push_back((int32_t)F.dep_idx.size());
+  }
+  F.n_entries = N;
+  // rows {count, the first kFlowDepRow - 1 sources, -1 ...}
+  const int K = bfly::kFlowDepRow;
+  F.deps.assign((size_t)N * K, -1);
+  for (int32_t e = 0; e < N; ++e) {
+    const int32_t n = F.dep_off[e + 1] - F.dep_off[e];
+    F.deps[(size_t)e * K] = n;
+    std::copy(F.dep_idx.begin() + F.dep_off[e], F.dep_idx.begin() + F.dep_off[e] + std::min(n, K - 1),
+              F.deps.begin() + (size_t)e * K + 1);
+  }
+  return "";
+}
+
+std::string build_flows(bfly_plan_t P) {
+  const int blocks = P->level_grid > 0 ? P->level_grid : 456;
+  std::string bad = build_flow(P, false, blocks, P->flowF);
+  if (bad.empty()) bad = build_flow(P, true, blocks, P->flowA);
+  return bad;
+}
+
+// Uploads the launch entries of both directions (they hold device pointers of the plan's
+// allocation) and clears the flags, epochs and work counters of the single-launch sweep.
+cudaError_t upload_flows(bfly_plan_t P) {
+  const int S = (int)P->steps.size();
+  P->fbuf[0] = P->buf[0];
+  P->fbuf[S] = P->buf[1];
+  for (int dir = 0; dir < 2; ++dir) {
+    bfly_plan_s::Flow &F = dir ? P->flowA : P->flowF;
+    std::vector<bfly::BatchEntry> ent;
+    ent.reserve((size_t)F.n_entries);
+    for (const auto &node : F.nodes) {
+      const int s = dir ? S - 1 - node.first : node.first;
+      const bfly_plan_s::Step &st = P->steps[s];
+      const int64_t hi = P->pairs[st.t + 1] * P->TS, lo = P->pairs[st.t - st.levels + 1] * P->TS;
+      const bfly::StageProgram &pg = dir ? P->progA[s] : P->progF[s];
+      const bfly_plan_s::DevProg &dp = dir ? P->dA[s] : P->dF[s];
+      bfly::BatchEntry be{};
+      be.d = pg.chunks[(size_t)node.second];
+      be.blob = dp.blob;
+      be.runs = dp.runs;
+      be.in = dir ? P->fbuf[s + 1] : P->fbuf[s];
+      be.out = dir ? P->fbuf[s] : P->fbuf[s + 1];
+      be.in_rhs = dir ? lo : hi;
+      be.out_rhs = dir ? hi : lo;
+      ent.push_back(be);
+    }
+    if ((int)ent.size() != F.n_entries) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemcpy(F.entries, ent.data(), ent.size() * sizeof(bfly::BatchEntry), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(F.flags, 0, (size_t)F.n_entries * P->max_nrhs * sizeof(unsigned));
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaMemset(P->epoch, 0, 2 * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(P->flow_sched, 0, 4 * sizeof(unsigned long long));
+  return e;
 }
 
 }  // namespace
@@ -143,6 +302,8 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   const bool rhs_groups = o.prec == BFLY_PREC_FP32 && (o.flags & BFLY_FLAG_RHS_GROUPS);
   if (rhs_groups && dim != 2)
     return fail(BFLY_ERR_UNSUPPORTED, "the right-hand-side grouped recursive step is built for dim = 2");
+  if ((o.flags & BFLY_FLAG_DATAFLOW) && (o.prec == BFLY_PREC_TC || rhs_groups))
+    return fail(BFLY_ERR_UNSUPPORTED, "the single-launch sweep runs the FP32 and FP64 recursive step");
   if (o.max_nrhs < 1 || o.max_nrhs > 4096) return fail(BFLY_ERR_INVALID_ARG, "max_nrhs must be in 1..4096");
   if (o.reserved != 0) return fail(BFLY_ERR_INVALID_ARG, "reserved options must be zero");
   if (o.stages < 0 || o.stages > bfly::kMaxLevels) return fail(BFLY_ERR_INVALID_ARG, "stages must be in 0..3");
@@ -406,6 +567,19 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   }
   P->steps = plan_steps;
   I.steps = (int)plan_steps.size();
+  if ((o.flags & BFLY_FLAG_DATAFLOW) && !plan_steps.empty()) {
+    if ((int64_t)I.chunks_fwd * o.max_nrhs >= INT32_MAX / 2) {
+      delete P;
+      return fail(BFLY_ERR_UNSUPPORTED, "the single-launch sweep numbers its items in 32 bits: fewer chunks x max_nrhs");
+    }
+    const std::string bad = build_flows(P);
+    if (!bad.empty()) {
+      delete P;
+      return fail(BFLY_ERR_CUDA, "internal error in the single-launch sweep: " + bad);
+    }
+    P->dataflow = true;
+    I.dataflow = 1;
+  }
   I.lane_use_fwd = lanes_issued_all ? (double)lanes_used_all / (double)lanes_issued_all : 1.0;
   if (host_only) {
     I.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -459,6 +633,24 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
   const size_t stage_bytes = (size_t)std::max(nx, nk) * 16 * o.max_nrhs;
   A.add(&P->stage_in, stage_bytes);
   A.add(&P->stage_out, stage_bytes);
+  if (P->dataflow) {
+    // a buffer per inner boundary of the sweep (boundary b: the last stage of step b - 1)
+    P->fbuf.assign(n_steps + 1, nullptr);
+    for (size_t b = 1; b < n_steps; ++b) {
+      const bfly_plan_s::Step &st = P->steps[b - 1];
+      A.add(&P->fbuf[b], (size_t)P->pairs[st.t - st.levels + 1] * P->TS * P->elem_bytes * o.max_nrhs);
+    }
+    for (bfly_plan_s::Flow *F : {&P->flowF, &P->flowA}) {
+      A.add(reinterpret_cast<void **>(&F->entries), (size_t)F->n_entries * sizeof(bfly::BatchEntry));
+      A.add_vec(&F->deps_d, F->deps);
+      A.add_vec(&F->dep_off_d, F->dep_off);
+      A.add_vec(&F->dep_idx_d, F->dep_idx);
+      A.add_vec(&F->first_use_d, F->first_use);
+      A.add(reinterpret_cast<void **>(&F->flags), (size_t)F->n_entries * o.max_nrhs * sizeof(unsigned));
+    }
+    A.add(reinterpret_cast<void **>(&P->epoch), 2 * sizeof(unsigned));
+    A.add(reinterpret_cast<void **>(&P->flow_sched), 4 * sizeof(unsigned long long));
+  }
 
   cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&P->dmem), A.total);
   if (e != cudaSuccess) {
@@ -476,6 +668,7 @@ bfly_status bfly_plan_create(bfly_plan_t *out, int dim, double N, int64_t nx, co
     }
     at += (it.bytes + 255) & ~(size_t)255;
   }
+  if (e == cudaSuccess && P->dataflow) e = upload_flows(P);
   if (e == cudaSuccess)
     e = bfly::launch_weights(o.prec == BFLY_PREC_FP64 ? 0 : 1, nk, dim, p, 0, P->off_k, P->inv_den, P->Wk, 0);
   if (e == cudaSuccess)
@@ -532,20 +725,34 @@ bfly_status run(bfly_plan_t P, const void *in, void *out, int nrhs, int dtype, b
     BFLY_CUDA(mark());
     BFLY_CUDA(P->ks->spread(point_args(P, false, in, P->buf[0], nrhs, io64, false,
                                        P->pairs[L] * PD), s));
-    // step 3: stages L-1 .. 0, one or two per launch
-    for (int si = 0; si < S; ++si) {
+    // step 3: stages L-1 .. 0, up to three per launch, or all in one launch
+    if (P->dataflow) {
       BFLY_CUDA(mark());
-      BFLY_CUDA(P->ks->level(level_args(P, si, false, nrhs), false, P->level_grid, P->level_smem, s));
+      BFLY_CUDA(P->ks->level(flow_args(P, false, nrhs), false, P->level_grid, P->level_smem, s));
+      for (int si = 1; si < S; ++si) BFLY_CUDA(mark());
+    } else {
+      for (int si = 0; si < S; ++si) {
+        BFLY_CUDA(mark());
+        BFLY_CUDA(P->ks->level(level_args(P, si, false, nrhs), false, P->level_grid, P->level_smem, s));
+      }
     }
     // step 4: evaluate at the targets from stage 0
     BFLY_CUDA(mark());
-    BFLY_CUDA(P->ks->interp(point_args(P, true, P->buf[S & 1], out, nrhs, io64, false, P->pairs[0] * PD), s));
+    BFLY_CUDA(P->ks->interp(point_args(P, true, P->buf[P->dataflow ? 1 : S & 1], out, nrhs, io64, false,
+                                       P->pairs[0] * PD), s));
   } else {
     BFLY_CUDA(mark());
-    BFLY_CUDA(P->ks->spread(point_args(P, true, in, P->buf[S & 1], nrhs, io64, true, P->pairs[0] * PD), s));
-    for (int si = S - 1; si >= 0; --si) {
+    BFLY_CUDA(P->ks->spread(point_args(P, true, in, P->buf[P->dataflow ? 1 : S & 1], nrhs, io64, true,
+                                       P->pairs[0] * PD), s));
+    if (P->dataflow) {
       BFLY_CUDA(mark());
-      BFLY_CUDA(P->ks->level(level_args(P, si, true, nrhs), true, P->level_grid, P->level_smem, s));
+      BFLY_CUDA(P->ks->level(flow_args(P, true, nrhs), true, P->level_grid, P->level_smem, s));
+      for (int si = 1; si < S; ++si) BFLY_CUDA(mark());
+    } else {
+      for (int si = S - 1; si >= 0; --si) {
+        BFLY_CUDA(mark());
+        BFLY_CUDA(P->ks->level(level_args(P, si, true, nrhs), true, P->level_grid, P->level_smem, s));
+      }
     }
     BFLY_CUDA(mark());
     BFLY_CUDA(P->ks->interp(point_args(P, false, P->buf[0], out, nrhs, io64, true,
@@ -918,6 +1125,8 @@ bfly_status autotune_create(bfly_plan_t *out, int dim, double N, int64_t nx, con
     if (c.prec >= 0) r.prec = c.prec;
     if (c.groups) r.flags |= BFLY_FLAG_RHS_GROUPS;
     else r.flags &= ~BFLY_FLAG_RHS_GROUPS;
+    // the single-launch sweep runs the FP32 and FP64 kernels only
+    if (c.groups || r.prec == BFLY_PREC_TC) r.flags &= ~BFLY_FLAG_DATAFLOW;
     return r;
   };
   const TuneChoice cached = cache_lookup(o.tune_cache, key);

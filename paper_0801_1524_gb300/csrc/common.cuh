@@ -126,6 +126,8 @@ __device__ __forceinline__ void store_io(void *p, int64_t i, C v, bool io64) {
 //   forward : in = stage t+1 charges, out = stage t charges;
 //   adjoint : in = stage t, out = stage t+1.
 // A stage buffer holds [rhs][tile][TS] complex values, TS = tile stride (level.cuh).
+constexpr int kFlowDepRow = 64;  // ints per entry in LevelArgs::deps
+
 struct LevelArgs {
   const void *in;
   void *out;
@@ -143,6 +145,17 @@ struct LevelArgs {
   // work counter of the launch {items taken after the first round, blocks done}: zero at
   // launch, reset by the last block to finish (one per stage and direction)
   unsigned long long *sched;
+  // Dataflow launch (all steps of a sweep in one launch; null otherwise).  Entries are the
+  // chunks of every step, step after step; entry e reads the outputs of the entries
+  // dep_idx[dep_off[e] .. dep_off[e + 1]) of the step before it, also held in the row
+  // deps[e * kFlowDepRow ..] = {count, the first kFlowDepRow - 1 of them, -1 ...}.
+  // flags[e * nrhs + r] holds the epoch of the last launch that published the outputs of
+  // item (e, r); the launch's epoch is *epoch + 1, and the last block to finish increments
+  // *epoch.
+  const int *deps, *dep_off, *dep_idx;
+  const int *first_use;  // per entry: the first entry that reads its outputs, -1 if none
+  unsigned *flags;
+  unsigned *epoch;
 };
 
 // Steps 2 and 4 and their adjoints: per-point weights against one tile per leaf.

@@ -151,7 +151,10 @@ struct Impl {
   using S = LevelShape<R, D, P>;
   static cudaError_t level(const LevelArgs &a, bool adjoint, int grid, size_t smem, cudaStream_t s) {
     if (a.nchunks <= 0) return cudaSuccess;
-    return launch_dependent(adjoint ? level_kernel<R, D, P, true> : level_kernel<R, D, P, false>,
+    if (a.deps)
+      return launch_dependent(adjoint ? level_kernel<R, D, P, true, true> : level_kernel<R, D, P, false, true>,
+                              dim3(grid), dim3(kLevelThreads), smem, s, a);
+    return launch_dependent(adjoint ? level_kernel<R, D, P, true, false> : level_kernel<R, D, P, false, false>,
                             dim3(grid), dim3(kLevelThreads), smem, s, a);
   }
   static cudaError_t level_setup(size_t smem, int *blocks) {
@@ -163,16 +166,18 @@ struct Impl {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(level_kernel<R, D, P, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(level_kernel<R, D, P, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    for (auto k : {level_kernel<R, D, P, false, false>, level_kernel<R, D, P, true, false>,
+                   level_kernel<R, D, P, false, true>, level_kernel<R, D, P, true, true>})
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e == cudaSuccess) e = init_operators<R>();
     if (e != cudaSuccess) return e;
     int b2 = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, level_kernel<R, D, P, false>, kLevelThreads, smem);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, level_kernel<R, D, P, true>, kLevelThreads, smem);
-    if (b2 < *blocks) *blocks = b2;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, level_kernel<R, D, P, false, false>, kLevelThreads, smem);
+    for (auto k : {level_kernel<R, D, P, true, false>, level_kernel<R, D, P, false, true>,
+                   level_kernel<R, D, P, true, true>}) {
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k, kLevelThreads, smem);
+      if (e == cudaSuccess && b2 < *blocks) *blocks = b2;
+    }
     return e;
   }
   static size_t level_smem(const ChunkCaps &c) { return S::bytes(c); }

@@ -128,6 +128,33 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 __device__ __forceinline__ void fence_async_shared() {
   asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
 }
+// Cross-block signalling of the dataflow launch: the bulk stores of an item's outputs
+// (async proxy) complete, a proxy fence orders them with the generic proxy, a release
+// fence and a store publish the item's flag; a reader that sees the flag takes an acquire
+// fence and fences the async proxy before its bulk copies of those outputs.
+__device__ __forceinline__ void fence_async_global() {
+  asm volatile("fence.proxy.async.global;\n" ::: "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(unsigned *p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_release_gpu() { asm volatile("fence.release.gpu;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_acquire_gpu() { asm volatile("fence.acquire.gpu;\n" ::: "memory"); }
+// Adds `bytes` to the transaction count of the current phase of `bar` (no arrival).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
@@ -321,7 +348,251 @@ __device__ __forceinline__ void run_pass(const Item *items, int n_items, int n_t
   }
 }
 
-template <typename R, int D, int P, bool ADJ>
+// Producer warp of a dataflow launch (LevelArgs::deps set: the chunks of every step of
+// a sweep in one launch).  Items come from the work counter in order, so that a block
+// only ever waits for items that running blocks hold (the grid's blocks need not all be
+// resident at once: blocks of kernels queued after this one may take the places of some);
+// each iteration also takes the next item, so a block holds at most one item it has not
+// started.  Iteration it, slot s = it mod 2:
+//   1. wait for the consumers to finish iteration it-2 and issue the stores of its outputs
+//      (the counter's latency overlaps them); load the next item's source list;
+//   2. copy the item's program; if one of its sources is not yet published, first publish
+//      everything this block holds (the outputs the consumers are computing included), then
+//      wait (bounded) for the sources: the lowest unfinished item then always has its
+//      sources, and the launch makes progress;
+//   3. copy the item's inputs;
+//   4. off the consumers' path: publish the written items (flag = the launch's epoch) once
+//      the counter comes near the first item that reads one of them (first_use); until
+//      then their stores complete unobserved.  Then look at the next item's sources.
+// Publishing waits for the block's stores to land and takes one release fence for all the
+// items it publishes; items that no later item reads are never published.
+constexpr int kFlowPending = 16;  // written items a block keeps unpublished at most
+template <typename R, int D, int P>
+__device__ __forceinline__ void flow_producer(const LevelArgs &a, uint64_t *full, uint64_t *staged, int *end_it,
+                                              unsigned char *meta0, typename Cx<R>::T *slot0,
+                                              typename Cx<R>::T *scr0, int lane) {
+  using C = typename Cx<R>::T;
+  using S = LevelShape<R, D, P>;
+  constexpr int TS = S::TS;
+  const int total = a.nchunks * a.nrhs;  // below 2^31 (checked by the plan)
+  int slot_it[2] = {-1, -1};       // iteration whose outputs slot s holds, -1: none
+  int slot_w[2] = {-1, -1};        // its work item
+  int phase_it[2] = {-1, -1};      // last iteration that completes a phase of full[s]
+  // written, unpublished items (lane j holds the j-th) and the smallest first_use among them
+  int pend_w = -1, n_pend = 0, pend_due = 0x7fffffff;
+  bool failed = false;
+  // the counter, the flags and every input follow the predecessor grid
+  pdl_wait();
+  const unsigned epoch = ld_acquire(a.epoch) + 1u;
+  auto publish_all = [&]() {
+    if (n_pend == 0) return;
+    bulk_wait_all();  // the stores have landed
+    fence_async_global();
+    __syncwarp();
+    fence_release_gpu();
+    if (lane < n_pend) st_relaxed(&a.flags[pend_w], epoch);
+    n_pend = 0;
+    pend_due = 0x7fffffff;
+    __syncwarp();
+  };
+  auto wait_staged = [&](int s, int prev) -> bool {
+    const bool ok = mbar_wait(&staged[s], (prev >> 1) & 1, a.wait_limit);
+    return __all_sync(0xffffffffu, ok);
+  };
+  // issues the stores of the outputs staged in slot s by item w (published later)
+  auto write_back = [&](int s, int w) {
+    if (n_pend == kFlowPending) publish_all();
+    const unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
+    const int32_t *hdr = reinterpret_cast<const int32_t *>(meta_s);
+    const int NP = hdr[0], n_oruns = hdr[2];
+    int n_items = 0;
+    for (int j = 0; j < NP; ++j) n_items += hdr[4 + j];
+    const Run *oruns = reinterpret_cast<const Run *>(meta_s + kBlobHeader + (size_t)n_items * sizeof(Item));
+    const C *stage_t = ((NP - 1) & 1) ? slot0 + (size_t)s * a.cap0 * TS : scr0 + (size_t)(s % S::NSCR) * a.cap1 * TS;
+    const unsigned char *stage = reinterpret_cast<const unsigned char *>(stage_t);
+    const int e = w / a.nrhs;
+    const BatchEntry &be = a.entries[e];
+    unsigned char *rout = reinterpret_cast<unsigned char *>(be.out) + (size_t)(w % a.nrhs) * be.out_rhs * sizeof(C);
+    for (int j = lane; j < n_oruns; j += 32) {
+      const Run rn = oruns[j];
+      bulk_s2g(rout + (size_t)rn.start * S::tile_bytes, stage + (size_t)rn.slot * S::tile_bytes,
+               (unsigned)(rn.count * S::tile_bytes));
+    }
+    bulk_commit();
+    bulk_wait_read();  // the slot may be refilled after this
+    __syncwarp();
+    const int fu = a.first_use[e];
+    if (fu >= 0) {  // read by a later item
+      if (lane == n_pend) pend_w = w;
+      ++n_pend;
+      if (fu < pend_due) pend_due = fu;
+    }
+  };
+  // the entries whose outputs item w reads, loaded early (their flags are read later):
+  // the entry's row {count, sources...} of LevelArgs::deps, lane j holding elements j and
+  // 32 + j (-1 past the count)
+  auto load_deps = [&](int w, int &d0, int &d1) {
+    d0 = d1 = -1;
+    if (w >= total) return;
+    const int *row = a.deps + (size_t)(w / a.nrhs) * kFlowDepRow;
+    d0 = row[lane];
+    d1 = row[32 + lane];
+  };
+  // whether every item whose outputs item w reads carries this launch's epoch
+  auto sources_ready = [&](int w, int d0, int d1) -> bool {
+    const int r = w % a.nrhs;
+    const int count = __shfl_sync(0xffffffffu, d0, 0);
+    if (count <= 0) return true;
+    bool ok = true;
+    if (count < kFlowDepRow) {
+      if (lane > 0 && d0 >= 0) ok = ld_relaxed(&a.flags[d0 * a.nrhs + r]) == epoch;
+      if (d1 >= 0) ok &= ld_relaxed(&a.flags[d1 * a.nrhs + r]) == epoch;
+    } else {
+      // more sources than a row holds: the full list
+      const int e = w / a.nrhs;
+      for (int j = a.dep_off[e] + lane; j < a.dep_off[e + 1]; j += 32)
+        ok &= ld_relaxed(&a.flags[a.dep_idx[j] * a.nrhs + r]) == epoch;
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (ok) {
+      // the sources' outputs are visible after the flags, to every lane
+      fence_acquire_gpu();
+      __syncwarp();
+    }
+    return ok;
+  };
+  int w = 0;
+  if (lane == 0) w = (int)min(atomicAdd(a.sched, 1ull), (unsigned long long)total);
+  w = __shfl_sync(0xffffffffu, w, 0);
+  int dep0, dep1;
+  load_deps(w, dep0, dep1);
+  bool ready = sources_ready(w, dep0, dep1);
+  int it = 0;
+  for (;; ++it) {
+    const int s = it & 1;
+    // 1.
+    const bool wb = slot_it[s] >= 0;
+    if (wb && !wait_staged(s, slot_it[s])) {
+      failed = true;
+      break;
+    }
+    int nxt = 0;
+    if (lane == 0) nxt = (int)min(atomicAdd(a.sched, 1ull), (unsigned long long)total);
+    if (wb) {
+      write_back(s, slot_w[s]);
+      slot_it[s] = -1;
+    }
+    const int w_next = __shfl_sync(0xffffffffu, nxt, 0);
+    int nd0, nd1;
+    load_deps(w_next, nd0, nd1);  // in flight while this item's copies are issued
+    if (w >= total) {
+      // no more work: the consumers stop at iteration it (the phase completes without data)
+      if (lane == 0) {
+        *end_it = it;
+        mbar_arrive(&full[s]);
+      }
+      phase_it[s] = it;
+      __syncwarp();
+      break;
+    }
+    const BatchEntry &be = a.entries[w / a.nrhs];
+    const ChunkDesc cd = be.d;
+    slot_it[s] = it;
+    slot_w[s] = w;
+    if (a.inject_stall && it == 0) {  // test hook: the first item never arrives
+      w = w_next;
+      dep0 = nd0;
+      dep1 = nd1;
+      ready = sources_ready(w, dep0, dep1);
+      continue;
+    }
+    // 2.
+    unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
+    unsigned char *in_s = reinterpret_cast<unsigned char *>(slot0 + (size_t)s * a.cap0 * TS);
+    if (lane == 0) {
+      mbar_expect_tx(&full[s], (unsigned)cd.blob_bytes);
+      bulk_g2s(meta_s, be.blob + cd.blob_off, (unsigned)cd.blob_bytes, &full[s]);
+    }
+    __syncwarp();
+    if (!ready && !(ready = sources_ready(w, dep0, dep1))) {
+      publish_all();
+      const int o = s ^ 1;
+      if (slot_it[o] >= 0) {
+        if (!wait_staged(o, slot_it[o])) failed = true;
+        else write_back(o, slot_w[o]);
+        slot_it[o] = -1;
+        publish_all();
+      }
+      // bounded wait (the decision to give up is the warp's, from lane 0's clock)
+      const long long t0 = clock64();
+      unsigned ns = 32;
+      while (!failed) {
+        ready = sources_ready(w, dep0, dep1);
+        if (ready || __shfl_sync(0xffffffffu, clock64() - t0 > a.wait_limit, 0)) break;
+        __nanosleep(ns);
+        if (ns < 512) ns *= 2;
+      }
+      if (!ready) {
+        // the consumers stop at this iteration once the program has landed
+        if (lane == 0) {
+          if (!failed) atomicOr(a.status, 8);
+          *end_it = it;
+          mbar_arrive(&full[s]);
+        }
+        slot_it[s] = -1;
+        phase_it[s] = it;
+        failed = true;
+        __syncwarp();
+        break;
+      }
+    }
+    // 3.
+    fence_async_global();
+    if (lane == 0) mbar_arrive_expect_tx(&full[s], (unsigned)(cd.n_in * (int)S::tile_bytes));
+    __syncwarp();
+    const unsigned char *rin =
+        reinterpret_cast<const unsigned char *>(be.in) + (size_t)(w % a.nrhs) * be.in_rhs * sizeof(C);
+    for (int j = lane; j < cd.n_runs; j += 32) {
+      const Run rn = be.runs[cd.run_off + j];
+      bulk_g2s(in_s + (size_t)rn.slot * S::tile_bytes, rin + (size_t)rn.start * S::tile_bytes,
+               (unsigned)(rn.count * S::tile_bytes), &full[s]);
+    }
+    phase_it[s] = it;
+    // 4. the blocks take about one item each while this one computes one: publish once
+    //    the counter is within two rounds of the grid of the first reader
+    if (n_pend > 0 && (long long)w_next + 2LL * gridDim.x >= (long long)pend_due * a.nrhs) publish_all();
+    w = w_next;
+    dep0 = nd0;
+    dep1 = nd1;
+    ready = sources_ready(w, dep0, dep1);
+  }
+  // the outputs of the iteration before the last
+  const int sl = (it + 1) & 1;
+  if (!failed && slot_it[sl] >= 0) {
+    if (wait_staged(sl, slot_it[sl])) write_back(sl, slot_w[sl]);
+    else failed = true;
+  }
+  publish_all();
+  if (failed && lane == 0) atomicOr(a.status, 1);
+  // copies still in flight land before the block exits
+  for (int s = 0; s < 2; ++s) {
+    const bool ok = phase_it[s] < 0 || mbar_wait(&full[s], (phase_it[s] >> 1) & 1, a.wait_limit);
+    if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicOr(a.status, 2);
+  }
+  bulk_wait_all();
+  if (lane == 0) {
+    // the last block done resets the counter and advances the epoch for the next launch
+    __threadfence();
+    if (atomicAdd(&a.sched[1], 1ull) == (unsigned long long)gridDim.x - 1) {
+      atomicExch(&a.sched[0], 0ull);
+      atomicExch(&a.sched[1], 0ull);
+      atomicAdd(a.epoch, 1u);
+    }
+  }
+}
+
+// FLOW: a dataflow launch (flow_producer drives the copies); else one launch per step.
+template <typename R, int D, int P, bool ADJ, bool FLOW>
 __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel(const LevelArgs a) {
   using C = typename Cx<R>::T;
   using S = LevelShape<R, D, P>;
@@ -357,6 +628,10 @@ __global__ void __launch_bounds__(kLevelThreads, kLevelBlocksPerSm) level_kernel
   unsigned char *gout = reinterpret_cast<unsigned char *>(a.out);
 
   if (warp == kConsumerWarps) {
+    if constexpr (FLOW) {
+      flow_producer<R, D, P>(a, full, staged, end_it, meta0, slot0, scr0, lane);
+      return;
+    }
     // ---------------- producer warp.  Work items w = chunk * nrhs + rhs, the chunks in
     // decreasing work: block b first takes item b, then the next untaken item of the
     // launch's counter (gridDim.x + a.sched[0]), so that the blocks finish together.

@@ -48,6 +48,24 @@ struct bfly_plan_s {
   // forward step s, b = steps: stage 0) lives in buf[b mod 2]
   void *buf[2] = {nullptr, nullptr};
   void *stage_in = nullptr, *stage_out = nullptr;
+  // single-launch sweep (BFLY_FLAG_DATAFLOW), per direction: the chunks of every step as
+  // launch entries (forward: step 0 first; adjoint: the last step first), entry e reading
+  // the outputs of entries dep_idx[dep_off[e] .. dep_off[e + 1]) (also as rows: deps,
+  // LevelArgs::deps); a flag per entry and right-hand side.  Boundary b of the sweep lives in fbuf[b] (fbuf[0] = buf[0],
+  // fbuf[steps] = buf[1], the others of their own).
+  struct Flow {
+    std::vector<int32_t> dep_off, dep_idx, deps, first_use;
+    std::vector<std::pair<int32_t, int32_t>> nodes;  // per entry: (step of the launch, chunk)
+    bfly::BatchEntry *entries = nullptr;
+    int32_t *deps_d = nullptr, *dep_off_d = nullptr, *dep_idx_d = nullptr, *first_use_d = nullptr;
+    unsigned *flags = nullptr;
+    int n_entries = 0;
+  };
+  bool dataflow = false;
+  Flow flowF, flowA;
+  std::vector<void *> fbuf;
+  unsigned *epoch = nullptr;                  // [2]: forward, adjoint (launches completed)
+  unsigned long long *flow_sched = nullptr;  // [2][2] work counters of the two launches
   bfly_plan_info_t info{};
 };
 
@@ -101,6 +119,26 @@ inline bfly::LevelArgs level_args(bfly_plan_t P, int s, bool adjoint, int nrhs) 
   a.status = P->status;
   a.inject_stall = stall ? 1 : 0;
   a.sched = P->sched + ((adjoint ? P->steps.size() : 0) + (size_t)s) * 2;
+  return a;
+}
+
+// Arguments of the single-launch sweep (BFLY_FLAG_DATAFLOW) in one direction.
+inline bfly::LevelArgs flow_args(bfly_plan_t P, bool adjoint, int nrhs) {
+  const bfly_plan_s::Flow &F = adjoint ? P->flowA : P->flowF;
+  bfly::LevelArgs a = level_args(P, 0, adjoint, nrhs);
+  a.in = a.out = nullptr;
+  a.chunks = nullptr;
+  a.blob = nullptr;
+  a.runs = nullptr;
+  a.entries = F.entries;
+  a.nchunks = F.n_entries;
+  a.sched = P->flow_sched + (adjoint ? 2 : 0);
+  a.deps = F.deps_d;
+  a.dep_off = F.dep_off_d;
+  a.dep_idx = F.dep_idx_d;
+  a.first_use = F.first_use_d;
+  a.flags = F.flags;
+  a.epoch = P->epoch + (adjoint ? 1 : 0);
   return a;
 }
 

@@ -17,6 +17,7 @@ BFLY_FLAG_TEST_STALL = 2
 BFLY_FLAG_AUTOTUNE = 4
 BFLY_FLAG_ONE_STAGE = 8
 BFLY_FLAG_RHS_GROUPS = 16
+BFLY_FLAG_DATAFLOW = 32
 
 # Every function the header declares, with (restype, argtypes).
 _vp, _i, _i64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
@@ -40,7 +41,8 @@ class PlanInfo(ctypes.Structure):
                 ("smem_kb", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("tuned_ms", ctypes.c_double),
                 ("plan_seconds", ctypes.c_double), ("steps", ctypes.c_int),
-                ("stages_per_launch", ctypes.c_int), ("rhs_groups", ctypes.c_int)]
+                ("stages_per_launch", ctypes.c_int), ("rhs_groups", ctypes.c_int),
+                ("dataflow", ctypes.c_int)]
 
 
 SIGNATURES = {

@@ -59,7 +59,8 @@ class Plan:
 
     def __init__(self, x, k, N: float, p: int, precision: str = "fp32", max_nrhs: int = 1,
                  host_only: bool = False, smem_kb: int = 0, flags: int = 0,
-                 autotune: bool = False, tune_cache: str | None = None, stages: int = 0):
+                 autotune: bool = False, tune_cache: str | None = None, stages: int = 0,
+                 dataflow: bool = False):
         lib = native.load()
         x = np.ascontiguousarray(x, dtype=np.float64)
         k = np.ascontiguousarray(k, dtype=np.float64)
@@ -78,7 +79,8 @@ class Plan:
         opts.max_nrhs = self.max_nrhs
         opts.flags = ((native.BFLY_FLAG_HOST_ONLY if host_only else 0) |
                       (native.BFLY_FLAG_AUTOTUNE if autotune else 0) |
-                      (native.BFLY_FLAG_RHS_GROUPS if precision == "fp32g" else 0) | int(flags))
+                      (native.BFLY_FLAG_RHS_GROUPS if precision == "fp32g" else 0) |
+                      (native.BFLY_FLAG_DATAFLOW if dataflow else 0) | int(flags))
         opts.smem_kb = int(smem_kb)
         opts.stages = int(stages)
         self._tune_cache = tune_cache.encode() if tune_cache else None
