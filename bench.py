@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--precision", default="fp32",
                     help="precision of the timed path (fp32, tc); star_batch: comma-separated "
                          "precisions of the batch, the first is the value")
+    ap.add_argument("--dataflow", choices=["auto", "on", "off"], default="auto",
+                    help="recursive step in one launch (BFLY_FLAG_DATAFLOW); auto: on for FP32 "
+                         "plans in 2D, where it is measured faster, off in 3D and for the "
+                         "tensor-core step")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and p = 9 companion measurements of the default run")
     return ap.parse_args()
@@ -210,10 +214,13 @@ def main_bfly(args, rank, world, dist):
     f_np = inst.sources(dtype=np.complex64, nrhs=nrhs).reshape(shp(nk))
     stream = torch.cuda.current_stream()
     f = torch.as_tensor(f_np, device=dev)
-    plan = Plan(inst.x, inst.k, inst.N, inst.p, precision=prec, smem_kb=args.smem_kb, max_nrhs=nrhs)
+    flow = args.dataflow == "on" or (args.dataflow == "auto" and inst.dim == 2 and prec == "fp32")
+    plan = Plan(inst.x, inst.k, inst.N, inst.p, precision=prec, smem_kb=args.smem_kb, max_nrhs=nrhs,
+                dataflow=flow)
     info = plan.info()
     L = info["L"]
-    S = info["steps"]    # recursive-step launches per transform
+    S = info["steps"]    # steps of the recursive step per transform (bfly_execute_events' marks)
+    SL = 1 if info["dataflow"] else S   # its launches
     u = torch.empty(shp(nx), dtype=torch.complex64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     alu = alu_peaks()
@@ -353,7 +360,7 @@ def main_bfly(args, rank, world, dist):
                            "eps_a_fp32_vs_gpu_direct_fp64": eps_a32}
         del plan64
 
-    # ---- roofline of the recursive step (the dominant kernel: S launches per step)
+    # ---- roofline of the recursive step (the dominant kernel: SL launches per step)
     d, p = inst.dim, inst.p
     PD = p ** d
     # algorithmic units of the recursive step, all stages, one RHS: per (pair, child)
@@ -366,12 +373,12 @@ def main_bfly(args, rank, world, dist):
     pairs = {t: a * b for t, a, b in plan.stages()}
     bytes_ = sum(pairs[t + 1] + pairs[t - lev + 1] for t, lev in steps) * PD * 8.0 * nrhs
     level_s = float(np.mean(level_ms)) * 1e-3
-    per_launch_s = level_s / S
+    per_launch_s = level_s / SL
     hbm_peak, hbm_src = peaks()
     alu_peak = alu["fp32x2"]   # TFLOP/s, measured in this run
-    a_alu = flops / S / per_launch_s / 1e12
-    a_exec = flops_exec / S / per_launch_s / 1e12
-    a_hbm = bytes_ / S / per_launch_s / 1e9
+    a_alu = flops / SL / per_launch_s / 1e12
+    a_exec = flops_exec / SL / per_launch_s / 1e12
+    a_hbm = bytes_ / SL / per_launch_s / 1e9
     roof_alu = {"bound": "alu", "achieved": a_alu, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": a_alu / alu_peak, "traffic": None,
                 "achieved_executed": a_exec, "frac_executed": a_exec / alu_peak,
@@ -383,22 +390,28 @@ def main_bfly(args, rank, world, dist):
     roof_hbm = {"bound": "hbm", "achieved": a_hbm, "peak": hbm_peak, "unit": "GB/s",
                 "frac": a_hbm / hbm_peak, "traffic": None,
                 "peak_source": f"{hbm_src} copy bandwidth"}
-    traffic = level_traffic(per_launch_bytes=bytes_ / S)
+    traffic = level_traffic(dataflow=bool(info["dataflow"]))
     main, alt = (roof_alu, roof_hbm) if roof_alu["frac"] >= roof_hbm["frac"] else (roof_hbm, roof_alu)
     main["traffic"] = traffic
     alt["traffic"] = traffic
     main["kernel"] = (("level_tc_kernel<" if prec == "tc" else "level_kernel<float,") + f"{d},{p}> "
-                      f"(recursive step, {S} launches of "
+                      + (f"(recursive step in one launch: {S} steps of " if info["dataflow"] else
+                         f"(recursive step, {S} launches of ")
                       + "/".join(str(lev) for _, lev in steps) + " stages)")
-    main["algorithmic_per_launch"] = {"flops": flops / S, "bytes": bytes_ / S,
-                                      "executed_flops": flops_exec / S}
+    main["algorithmic_per_launch"] = {"flops": flops / SL, "bytes": bytes_ / SL,
+                                      "executed_flops": flops_exec / SL}
     main["duration"] = ("mean per-launch CUDA-event time of the recursive step, from a second pass "
                         "of the same steps with an event between consecutive launches")
     alt["kernel"] = main["kernel"]
     out["roofline_alt"] = alt
     kern_names = (["leaf"] + [f"level_t{t}" + (f"-{t - lev + 1}" if lev > 1 else "") for t, lev in steps]
                   + ["final"])
-    out["kernel_ms"] = {n: float(v) for n, v in zip(kern_names, kern_ms.mean(axis=0))}
+    km = kern_ms.mean(axis=0)
+    if info["dataflow"]:   # one launch: the marks between its steps are back to back
+        out["kernel_ms"] = {"leaf": float(km[0]), f"level_t{L - 1}-0": float(km[1:S + 1].sum()),
+                            "final": float(km[S + 1])}
+    else:
+        out["kernel_ms"] = {n: float(v) for n, v in zip(kern_names, km)}
 
     value = replica_value(world, ms) * nrhs   # right-hand sides transformed per second
     line = {
@@ -408,7 +421,9 @@ def main_bfly(args, rank, world, dist):
         "config": {**describe(inst, nrhs), "parallelism": f"replicas{world}" if world > 1 else "single GPU",
                    "precision": "FP32 applies, FP64-built operators and weights" if prec == "fp32" else
                    "recursive step on the tensor cores (TF32 operands split hi + lo, FP32 accumulation), "
-                   "FP32 leaf and final steps"},
+                   "FP32 leaf and final steps",
+                   "recursive_step": (f"one launch for its {S} steps (BFLY_FLAG_DATAFLOW)" if info["dataflow"]
+                                      else f"{S} launches")},
         "ms_stats": {"mean": float(np.mean(step_ms)), "median": float(np.median(step_ms)),
                      "min": float(np.min(step_ms)), "max": float(np.max(step_ms)), "rank": rank},
         "effective_IJ_per_s": value * nx * nk,
@@ -419,7 +434,7 @@ def main_bfly(args, rank, world, dist):
         "roofline": main,
         "adjoint": {"ms": float(np.mean(adj_ms)), "transforms_per_s": 1e3 / float(np.mean(adj_ms)),
                     "call": "bfly_execute_adjoint (device buffers; the sweep behind the gradient)"},
-        "gpu_launches": args.steps * (S + 2),
+        "gpu_launches": args.steps * (SL + 2),
         "clocks": clk,
         "plan": {"seconds": info["plan_seconds"], "L": L, "total_pairs": info["total_pairs"],
                  "max_pairs": info["max_pairs"], "workspace_bytes": info["workspace_bytes"]},
@@ -451,9 +466,9 @@ def main_bfly(args, rank, world, dist):
     return line
 
 
-def level_traffic(per_launch_bytes):
-    """DRAM bytes per recursive-step launch from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
+def level_traffic(dataflow):
+    """DRAM bytes per recursive-step launch (the one launch of the sweep with dataflow) from
+    the committed ncu summary, if it was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "level_traffic.json")
     try:
         with open(path) as fh:
@@ -461,7 +476,7 @@ def level_traffic(per_launch_bytes):
         import hashlib
         src = os.path.join(ROOT, "paper_0801_1524_gb300", "csrc", "level.cuh")
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if d.get("level_cuh_sha256_16") != h:
+        if d.get("level_cuh_sha256_16") != h or bool(d.get("dataflow", False)) != dataflow:
             return None
         return float(d["dram_bytes_per_launch"])
     except Exception:

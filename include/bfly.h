@@ -65,10 +65,12 @@ typedef enum { BFLY_PREC_FP64 = 0, BFLY_PREC_FP32 = 1, BFLY_PREC_TC = 2 } bfly_p
  * SM) x the stages per launch (2D: 3, 2, 1; 3D: one); for an FP32 plan in 2D with
  * max_nrhs >= 4, the right-hand-side grouped step (BFLY_FLAG_RHS_GROUPS) at two budgets
  * and two stage counts; with max_nrhs >= 8 also the tensor-core recursive step
- * (BFLY_PREC_TC) at two budgets and two stage counts.  With tune_cache set, a choice recorded there for the same GPU, dim, p,
- * requested precision, nrhs and size class is reused, and new choices are appended.
- * bfly_plan_info_t reports the chosen precision, budget, stages and whether the
- * right-hand sides are grouped (rhs_groups). */
+ * (BFLY_PREC_TC) at two budgets and two stage counts; then the best FP32 or FP64
+ * candidate with the single-launch sweep (BFLY_FLAG_DATAFLOW) switched the other way.
+ * With tune_cache set, a choice recorded there for the same GPU, dim, p, requested
+ * precision, nrhs and size class is reused, and new choices are appended.
+ * bfly_plan_info_t reports the chosen precision, budget, stages, whether the right-hand
+ * sides are grouped (rhs_groups) and whether the sweep runs in one launch (dataflow). */
 #define BFLY_FLAG_AUTOTUNE 4u
 /* One stage per launch of the recursive step also in 2D (no stages fused in shared
  * memory): the unfused programs of Sec. 2.2 step 3, for comparison and testing. */

@@ -1047,10 +1047,11 @@ std::string tune_key(int dim, int p, int prec, int nrhs, int64_t max_pairs) {
 // launch (2D), precision of the applies.
 struct TuneChoice {
   int smem_kb = 0, stages = 0, prec = -1, groups = 0;  // groups: BFLY_FLAG_RHS_GROUPS
+  int flow = -1;  // BFLY_FLAG_DATAFLOW: 1 on, 0 off, -1 as requested
 };
 
-// The last choice recorded for `key` ("<key> <smem_kb> [<stages> <prec>]" lines), or
-// smem_kb = 0 when there is none.
+// The last choice recorded for `key` ("<key> <smem_kb> [<stages> <prec> [<groups>
+// [<flow>]]]" lines), or smem_kb = 0 when there is none.
 TuneChoice cache_lookup(const char *path, const std::string &key) {
   TuneChoice found;
   if (!path) return found;
@@ -1061,10 +1062,12 @@ TuneChoice cache_lookup(const char *path, const std::string &key) {
     std::string l(line);
     if (l.compare(0, key.size(), key) != 0 || l.size() <= key.size() || l[key.size()] != ' ') continue;
     TuneChoice c;
-    const int n = std::sscanf(l.c_str() + key.size(), " %d %d %d %d", &c.smem_kb, &c.stages, &c.prec, &c.groups);
+    const int n = std::sscanf(l.c_str() + key.size(), " %d %d %d %d %d", &c.smem_kb, &c.stages, &c.prec, &c.groups,
+                              &c.flow);
     if (n >= 1 && c.smem_kb > 0) {
       if (n < 3) c.stages = 0, c.prec = -1;
       if (n < 4) c.groups = 0;
+      if (n < 5) c.flow = -1;
       found = c;
     }
   }
@@ -1076,7 +1079,7 @@ void cache_store(const char *path, const std::string &key, const TuneChoice &c) 
   if (!path) return;
   FILE *fh = std::fopen(path, "a");
   if (!fh) return;
-  std::fprintf(fh, "%s %d %d %d %d\n", key.c_str(), c.smem_kb, c.stages, c.prec, c.groups);
+  std::fprintf(fh, "%s %d %d %d %d %d\n", key.c_str(), c.smem_kb, c.stages, c.prec, c.groups, c.flow);
   std::fclose(fh);
 }
 
@@ -1125,6 +1128,8 @@ bfly_status autotune_create(bfly_plan_t *out, int dim, double N, int64_t nx, con
     if (c.prec >= 0) r.prec = c.prec;
     if (c.groups) r.flags |= BFLY_FLAG_RHS_GROUPS;
     else r.flags &= ~BFLY_FLAG_RHS_GROUPS;
+    if (c.flow == 1) r.flags |= BFLY_FLAG_DATAFLOW;
+    if (c.flow == 0) r.flags &= ~BFLY_FLAG_DATAFLOW;
     // the single-launch sweep runs the FP32 and FP64 kernels only
     if (c.groups || r.prec == BFLY_PREC_TC) r.flags &= ~BFLY_FLAG_DATAFLOW;
     return r;
@@ -1180,6 +1185,25 @@ bfly_status autotune_create(bfly_plan_t *out, int dim, double N, int64_t nx, con
     }
   }
   if (!best) return fail(BFLY_ERR_UNSUPPORTED, "autotuning: no candidate configuration could be built");
+  // the best FP32 / FP64 configuration with the single-launch sweep switched the other way
+  best_c.flow = best->dataflow ? 1 : 0;
+  if (best->prec != BFLY_PREC_TC && !best_c.groups) {
+    TuneChoice c = best_c;
+    c.flow = 1 - best_c.flow;
+    const bfly_opts r = with(c);
+    bfly_plan_t P = nullptr;
+    double ms = 0;
+    if (bfly_plan_create(&P, dim, N, nx, x, nk, k, p, &r) == BFLY_OK) {
+      if (time_plan(P, &ms) == BFLY_OK && ms < best_ms) {
+        bfly_plan_destroy(best);
+        best = P;
+        best_ms = ms;
+        best_c = c;
+      } else {
+        bfly_plan_destroy(P);
+      }
+    }
+  }
   best->info.tuned_ms = best_ms;
   cache_store(o.tune_cache, key, best_c);
   g_err.clear();

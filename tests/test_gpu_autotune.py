@@ -24,7 +24,7 @@ PREC = {native.BFLY_PREC_FP32: "fp32", native.BFLY_PREC_TC: "tc", native.BFLY_PR
 def _chosen(plan):
     i = plan.info()
     prec = "fp32g" if i["rhs_groups"] else PREC[i["prec"]]
-    return dict(smem_kb=i["smem_kb"], stages=i["stages_per_launch"], precision=prec)
+    return dict(smem_kb=i["smem_kb"], stages=i["stages_per_launch"], precision=prec, dataflow=bool(i["dataflow"]))
 
 
 @pytest.mark.parametrize("nrhs", [2, 16])
