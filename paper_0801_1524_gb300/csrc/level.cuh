@@ -351,19 +351,19 @@ __device__ __forceinline__ void run_pass(const Item *items, int n_items, int n_t
 // Producer warp of a dataflow launch (LevelArgs::deps set: the chunks of every step of
 // a sweep in one launch).  Items come from the work counter in order, so that a block
 // only ever waits for items that running blocks hold (the grid's blocks need not all be
-// resident at once: blocks of kernels queued after this one may take the places of some);
-// each iteration also takes the next item, so a block holds at most one item it has not
-// started.  Iteration it, slot s = it mod 2:
-//   1. wait for the consumers to finish iteration it-2 and issue the stores of its outputs
-//      (the counter's latency overlaps them); load the next item's source list;
+// resident at once: blocks of kernels queued after this one may take the places of some).
+// An item is taken only when its slot is free (taking it one iteration ahead, to hide the
+// counter's latency, measured slower: the items in flight then reach further ahead of the
+// published ones, and more of them wait).  Iteration it, slot s = it mod 2:
+//   1. wait for the consumers to finish iteration it-2, take the item (the counter's
+//      latency overlaps the stores of that iteration's outputs); publish the written
+//      items (flag = the launch's epoch) once the counter comes near the first item that
+//      reads one of them (first_use), until then their stores complete unobserved;
 //   2. copy the item's program; if one of its sources is not yet published, first publish
 //      everything this block holds (the outputs the consumers are computing included), then
 //      wait (bounded) for the sources: the lowest unfinished item then always has its
 //      sources, and the launch makes progress;
-//   3. copy the item's inputs;
-//   4. off the consumers' path: publish the written items (flag = the launch's epoch) once
-//      the counter comes near the first item that reads one of them (first_use); until
-//      then their stores complete unobserved.  Then look at the next item's sources.
+//   3. copy the item's inputs.
 // Publishing waits for the block's stores to land and takes one release fence for all the
 // items it publishes; items that no later item reads are never published.
 constexpr int kFlowPending = 16;  // written items a block keeps unpublished at most
@@ -461,12 +461,7 @@ __device__ __forceinline__ void flow_producer(const LevelArgs &a, uint64_t *full
     }
     return ok;
   };
-  int w = 0;
-  if (lane == 0) w = (int)min(atomicAdd(a.sched, 1ull), (unsigned long long)total);
-  w = __shfl_sync(0xffffffffu, w, 0);
-  int dep0, dep1;
-  load_deps(w, dep0, dep1);
-  bool ready = sources_ready(w, dep0, dep1);
+  int w = 0, dep0 = -1, dep1 = -1;
   int it = 0;
   for (;; ++it) {
     const int s = it & 1;
@@ -482,9 +477,12 @@ __device__ __forceinline__ void flow_producer(const LevelArgs &a, uint64_t *full
       write_back(s, slot_w[s]);
       slot_it[s] = -1;
     }
-    const int w_next = __shfl_sync(0xffffffffu, nxt, 0);
-    int nd0, nd1;
-    load_deps(w_next, nd0, nd1);  // in flight while this item's copies are issued
+    w = __shfl_sync(0xffffffffu, nxt, 0);
+    // the blocks take about one item each while this one computes one: publish the written
+    // items once the counter is within two rounds of the grid of the first reader (before
+    // this item's copies: a reader may be waiting)
+    if (n_pend > 0 && (long long)w + 2LL * gridDim.x >= (long long)pend_due * a.nrhs) publish_all();
+    load_deps(w, dep0, dep1);
     if (w >= total) {
       // no more work: the consumers stop at iteration it (the phase completes without data)
       if (lane == 0) {
@@ -499,13 +497,7 @@ __device__ __forceinline__ void flow_producer(const LevelArgs &a, uint64_t *full
     const ChunkDesc cd = be.d;
     slot_it[s] = it;
     slot_w[s] = w;
-    if (a.inject_stall && it == 0) {  // test hook: the first item never arrives
-      w = w_next;
-      dep0 = nd0;
-      dep1 = nd1;
-      ready = sources_ready(w, dep0, dep1);
-      continue;
-    }
+    if (a.inject_stall && it == 0) continue;  // test hook: the first item never arrives
     // 2.
     unsigned char *meta_s = meta0 + (size_t)s * a.meta_bytes;
     unsigned char *in_s = reinterpret_cast<unsigned char *>(slot0 + (size_t)s * a.cap0 * TS);
@@ -514,7 +506,8 @@ __device__ __forceinline__ void flow_producer(const LevelArgs &a, uint64_t *full
       bulk_g2s(meta_s, be.blob + cd.blob_off, (unsigned)cd.blob_bytes, &full[s]);
     }
     __syncwarp();
-    if (!ready && !(ready = sources_ready(w, dep0, dep1))) {
+    bool ready = sources_ready(w, dep0, dep1);
+    if (!ready) {
       publish_all();
       const int o = s ^ 1;
       if (slot_it[o] >= 0) {
@@ -558,13 +551,6 @@ __device__ __forceinline__ void flow_producer(const LevelArgs &a, uint64_t *full
                (unsigned)(rn.count * S::tile_bytes), &full[s]);
     }
     phase_it[s] = it;
-    // 4. the blocks take about one item each while this one computes one: publish once
-    //    the counter is within two rounds of the grid of the first reader
-    if (n_pend > 0 && (long long)w_next + 2LL * gridDim.x >= (long long)pend_due * a.nrhs) publish_all();
-    w = w_next;
-    dep0 = nd0;
-    dep1 = nd1;
-    ready = sources_ready(w, dep0, dep1);
   }
   // the outputs of the iteration before the last
   const int sl = (it + 1) & 1;
