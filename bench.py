@@ -390,7 +390,7 @@ def main_bfly(args, rank, world, dist):
     roof_hbm = {"bound": "hbm", "achieved": a_hbm, "peak": hbm_peak, "unit": "GB/s",
                 "frac": a_hbm / hbm_peak, "traffic": None,
                 "peak_source": f"{hbm_src} copy bandwidth"}
-    traffic = level_traffic(dataflow=bool(info["dataflow"]))
+    traffic = level_traffic(dataflow=bool(info["dataflow"]), steps=steps)
     main, alt = (roof_alu, roof_hbm) if roof_alu["frac"] >= roof_hbm["frac"] else (roof_hbm, roof_alu)
     main["traffic"] = traffic
     alt["traffic"] = traffic
@@ -466,9 +466,10 @@ def main_bfly(args, rank, world, dist):
     return line
 
 
-def level_traffic(dataflow):
+def level_traffic(dataflow, steps):
     """DRAM bytes per recursive-step launch (the one launch of the sweep with dataflow) from
-    the committed ncu summary, if it was taken on the current kernel source; else None."""
+    the committed ncu summary, if it was taken on the current kernel source and the same
+    steps; else None."""
     path = os.path.join(ROOT, "profiles", "level_traffic.json")
     try:
         with open(path) as fh:
@@ -477,6 +478,8 @@ def level_traffic(dataflow):
         src = os.path.join(ROOT, "paper_0801_1524_gb300", "csrc", "level.cuh")
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         if d.get("level_cuh_sha256_16") != h or bool(d.get("dataflow", False)) != dataflow:
+            return None
+        if [list(x) for x in d.get("steps", [])] != [list(x) for x in steps]:
             return None
         return float(d["dram_bytes_per_launch"])
     except Exception:

@@ -106,8 +106,9 @@ typedef struct {
                               (2D: 72 KB FP32, 55 KB FP64; 3D: 73 KB; BFLY_PREC_TC: 110 KB) */
   const char *tune_cache;  /* autotuning cache file (text), or NULL */
   int stages;              /* at most this many stages per launch of the recursive step:
-                              2D 1..3 (0 = default 3), 3D 1..2 (0 = default 1; larger
-                              values are taken as 2); BFLY_FLAG_ONE_STAGE sets 1 */
+                              2D 1..3 (0 = default 3, or 2 with BFLY_FLAG_DATAFLOW), 3D 1..2
+                              (0 = default 1; larger values are taken as 2);
+                              BFLY_FLAG_ONE_STAGE sets 1 */
   int reserved;            /* must be zero */
 } bfly_opts;
 

@@ -18,10 +18,13 @@ pytestmark = pytest.mark.gpu
 
 
 def _pair(inst, prec, nrhs, **kw):
+    # the same steps launched one by one (a) and in one launch (b)
     from paper_0801_1524_gb300.plan import Plan
-    a = Plan(inst.x, inst.k, inst.N, inst.p, precision=prec, max_nrhs=nrhs, **kw)
     b = Plan(inst.x, inst.k, inst.N, inst.p, precision=prec, max_nrhs=nrhs, dataflow=True, **kw)
+    a = Plan(inst.x, inst.k, inst.N, inst.p, precision=prec, max_nrhs=nrhs,
+             stages=b.info()["stages_per_launch"], **kw)
     assert b.info()["dataflow"] == 1 and a.info()["dataflow"] == 0
+    assert a.steps() == b.steps()
     return a, b
 
 
@@ -61,8 +64,9 @@ def test_curve_matches_oracle_and_step_by_step(prec):
     from paper_0801_1524_gb300.plan import Plan
     x = w.sample_curve(w.circle_curve(), 2048.0)
     k = w.sample_curve(w.star_curve(3), 2048.0)
-    a = Plan(x, k, 2048.0, 7, precision=prec, max_nrhs=2)
     b = Plan(x, k, 2048.0, 7, precision=prec, max_nrhs=2, dataflow=True)
+    a = Plan(x, k, 2048.0, 7, precision=prec, max_nrhs=2, stages=b.info()["stages_per_launch"])
+    assert b.info()["stages_per_launch"] == 2 and a.steps() == b.steps()
     f = w.gaussian_sources(k.shape[0], nrhs=2, seed=9)
     dt = torch.complex64 if prec == "fp32" else torch.complex128
     ft = torch.as_tensor(f, dtype=dt, device="cuda")
