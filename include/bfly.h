@@ -66,7 +66,8 @@ typedef enum { BFLY_PREC_FP64 = 0, BFLY_PREC_FP32 = 1, BFLY_PREC_TC = 2 } bfly_p
  * max_nrhs >= 4, the right-hand-side grouped step (BFLY_FLAG_RHS_GROUPS) at two budgets
  * and two stage counts; with max_nrhs >= 8 also the tensor-core recursive step
  * (BFLY_PREC_TC) at two budgets and two stage counts; then the best FP32 or FP64
- * candidate with the single-launch sweep (BFLY_FLAG_DATAFLOW) switched the other way.
+ * candidate with the single-launch sweep (BFLY_FLAG_DATAFLOW) switched the other way (on,
+ * in 2D: at two and three stages per step).
  * With tune_cache set, a choice recorded there for the same GPU, dim, p, requested
  * precision, nrhs and size class is reused, and new choices are appended.
  * bfly_plan_info_t reports the chosen precision, budget, stages, whether the right-hand

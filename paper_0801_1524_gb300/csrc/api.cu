@@ -1191,19 +1191,30 @@ bfly_status autotune_create(bfly_plan_t *out, int dim, double N, int64_t nx, con
   }
   if (!best) return fail(BFLY_ERR_UNSUPPORTED, "autotuning: no candidate configuration could be built");
   // the best FP32 / FP64 configuration with the single-launch sweep switched the other way
+  // (switched on in 2D: at two and three stages per step, unless the stages were given)
   best_c.flow = best->dataflow ? 1 : 0;
   if (best->prec != BFLY_PREC_TC && !best_c.groups) {
+    std::vector<TuneChoice> flips;
     TuneChoice c = best_c;
     c.flow = 1 - best_c.flow;
-    const bfly_opts r = with(c);
-    bfly_plan_t P = nullptr;
-    double ms = 0;
-    if (bfly_plan_create(&P, dim, N, nx, x, nk, k, p, &r) == BFLY_OK) {
+    if (c.flow == 1 && dim == 2 && !fixed_stages) {
+      for (int stg : {2, 3}) {
+        c.stages = stg;
+        flips.push_back(c);
+      }
+    } else {
+      flips.push_back(c);
+    }
+    for (const TuneChoice &f : flips) {
+      const bfly_opts r = with(f);
+      bfly_plan_t P = nullptr;
+      double ms = 0;
+      if (bfly_plan_create(&P, dim, N, nx, x, nk, k, p, &r) != BFLY_OK) continue;
       if (time_plan(P, &ms) == BFLY_OK && ms < best_ms) {
         bfly_plan_destroy(best);
         best = P;
         best_ms = ms;
-        best_c = c;
+        best_c = f;
       } else {
         bfly_plan_destroy(P);
       }
