@@ -161,3 +161,35 @@ def test_program_export_sizes_and_errors():
     assert lib.bfly_plan_program(P._h, P.info()["steps"], 0, 0, None, 0, ctypes.byref(n)) == native.BFLY_ERR_INVALID_ARG
     assert lib.bfly_plan_program(P._h, 0, 0, 3, None, 0, ctypes.byref(n)) == native.BFLY_ERR_INVALID_ARG
     assert lib.bfly_plan_program(None, 0, 0, 0, None, 0, ctypes.byref(n)) == native.BFLY_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("dim,N,p", [(2, 1.0, 5), (2, 2.0, 5), (2, 16.0, 7), (2, 1000.5, 7), (3, 16.0, 5),
+                                     (3, 12.0, 3)])
+def test_dataflow_plans_build(dim, N, p):
+    # BFLY_FLAG_DATAFLOW: the launch entries and the source lists of every chunk (and their
+    # checks: every input tile written by a chunk of the step before, every chunk after its
+    # sources) are built at plan creation, also for a host-only plan
+    inst = w.small_random(dim, N, p, 200, 150, 9, edge_fraction=0.3)
+    P = Plan(inst.x, inst.k, N, p, host_only=True, dataflow=True)
+    info = P.info()
+    assert info["dataflow"] == (1 if info["steps"] > 0 else 0)
+    if dim == 2 and info["L"] > 1:
+        assert info["stages_per_launch"] == 2     # the default with the flag in 2D
+        Q = Plan(inst.x, inst.k, N, p, host_only=True, dataflow=True, stages=3)
+        assert Q.info()["stages_per_launch"] == 3 and Q.info()["dataflow"] == 1
+    plain = Plan(inst.x, inst.k, N, p, host_only=True, stages=info["stages_per_launch"])
+    assert plain.steps() == P.steps() and plain.info()["dataflow"] == 0
+
+
+@pytest.mark.parametrize("nx,nk", [(0, 40), (40, 0)])
+def test_dataflow_with_an_empty_side(nx, nk):
+    P = Plan(w.random_points(nx, 64.0, 2, 1), w.random_points(nk, 64.0, 2, 2), 64.0, 5, host_only=True,
+             dataflow=True)
+    assert P.info()["chunks_fwd"] == 0
+
+
+def test_dataflow_refused_with_tensor_cores_and_groups():
+    inst = w.small_random(2, 64.0, 7, 300, 300, 41)
+    for prec in ("tc", "fp32g"):
+        with pytest.raises(native.BflyError):
+            Plan(inst.x, inst.k, inst.N, inst.p, precision=prec, max_nrhs=8, host_only=True, dataflow=True)
