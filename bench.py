@@ -466,6 +466,16 @@ def main_bfly(args, rank, world, dist):
     return line
 
 
+def level_code_hash():
+    """sha256 (16 hex digits) of the recursive step's kernel source without its comments and
+    blank lines: the key of the committed DRAM-traffic summary."""
+    import hashlib
+    import re
+    src = open(os.path.join(ROOT, "paper_0801_1524_gb300", "csrc", "level.cuh")).read()
+    lines = [re.sub(r"//.*$", "", ln).rstrip() for ln in src.splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()[:16]
+
+
 def level_traffic(dataflow, steps):
     """DRAM bytes per recursive-step launch (the one launch of the sweep with dataflow) from
     the committed ncu summary, if it was taken on the current kernel source and the same
@@ -474,10 +484,7 @@ def level_traffic(dataflow, steps):
     try:
         with open(path) as fh:
             d = json.load(fh)
-        import hashlib
-        src = os.path.join(ROOT, "paper_0801_1524_gb300", "csrc", "level.cuh")
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if d.get("level_cuh_sha256_16") != h or bool(d.get("dataflow", False)) != dataflow:
+        if d.get("level_cuh_code_sha256_16") != level_code_hash() or bool(d.get("dataflow", False)) != dataflow:
             return None
         if [list(x) for x in d.get("steps", [])] != [list(x) for x in steps]:
             return None

@@ -1,5 +1,6 @@
-// Recursive step of the butterfly (Sec. 2.2 step 3, Fig. 1), one launch per step of one
-// stage or (2D) two consecutive stages.
+// Recursive step of the butterfly (Sec. 2.2 step 3, Fig. 1): one launch per step of up to
+// three consecutive stages (2D; one in 3D), or all steps in one launch whose chunks wait
+// for the chunks they read (the dataflow launch, flow_producer below).
 //
 // For every pair (A, B) at stage t the charges are
 //     f^{AB} = sum_{c in children(B)} ( (x)_d T^{(alpha_d(A), delta_d(c))} ) f^{A' Bc}
