@@ -94,7 +94,8 @@ typedef enum { BFLY_PREC_FP64 = 0, BFLY_PREC_FP32 = 1, BFLY_PREC_TC = 2 } bfly_p
  * sweep this way (bfly_execute_events then records its events between the recursive
  * step's steps back to back, after the one launch); the split, no-allocation and batch
  * entry points launch step by step as without the flag.  The results are bit-identical
- * to those of the step-by-step launches.  BFLY_ERR_UNSUPPORTED with BFLY_PREC_TC or
+ * to those of the same steps launched one by one (in 2D the flag makes two stages per step
+ * the default: a plan without it built with stages = 2).  BFLY_ERR_UNSUPPORTED with BFLY_PREC_TC or
  * BFLY_FLAG_RHS_GROUPS; with BFLY_FLAG_AUTOTUNE, candidates on those steps are built
  * without it. */
 #define BFLY_FLAG_DATAFLOW 32u
